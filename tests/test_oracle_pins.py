@@ -1,0 +1,450 @@
+"""Pins of the oracle against facts that do not come from the oracle itself:
+brute force, closed forms, published check values and the paper's stated
+numbers (Eq. 1, Eq. 2, Sec. II-A/B, Sec. III, Table I, Fig. 3)."""
+from itertools import permutations, product
+
+import mpmath as mp
+import numpy as np
+import pytest
+
+from paper_1911_08868_gb300 import inputs
+
+POLY8, POLY24 = 0x9B, 0x1B2B117
+
+
+def kron_G(n):
+    F = np.array([[1, 0], [1, 1]], dtype=np.int64)
+    G = np.array([[1]], dtype=np.int64)
+    for _ in range(n):
+        G = np.kron(G, F)
+    return G
+
+
+# --------------------------------------------------------------- Eq. 1
+def test_encoder_is_kronecker_power_n8_exhaustive(oracle):
+    G = kron_G(3)
+    for u in product([0, 1], repeat=8):
+        u = np.array(u, dtype=np.uint8)
+        assert np.array_equal(oracle.encode(u), (u.astype(np.int64) @ G) % 2)
+
+
+def test_encoder_is_kronecker_power_n16_sampled(oracle):
+    G = kron_G(4)
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        u = rng.integers(0, 2, 16).astype(np.uint8)
+        assert np.array_equal(oracle.encode(u), (u.astype(np.int64) @ G) % 2)
+
+
+# --------------------------------------------------------------- Sec. III: permuted graphs
+def _graph_matrix(oracle, n, sb):
+    N = 1 << n
+    M = np.zeros((N, N), dtype=np.int64)
+    for j in range(N):
+        e = np.zeros(N, dtype=np.uint8)
+        e[j] = 1
+        M[j] = oracle.graph_encode(n, sb, e)
+    return M
+
+
+def test_every_full_stage_order_encodes_G_n3(oracle):
+    G = kron_G(3)
+    for order in permutations(range(3)):
+        sb = oracle.graph_from_event(3, oracle.Event.make(1, 3, 0, order))
+        assert np.array_equal(_graph_matrix(oracle, 3, sb), G)
+
+
+def test_every_partial_permutation_encodes_G_n4(oracle):
+    n, G = 4, kron_G(4)
+    count = 0
+    for rng_ in range(2, n + 1):
+        for level in range(1, n - rng_ + 2):
+            m = level + rng_ - 1
+            for block in range((1 << n) >> m):
+                for order in permutations(range(rng_)):
+                    sb = oracle.graph_from_event(n, oracle.Event.make(level, rng_, block, order))
+                    assert np.array_equal(_graph_matrix(oracle, n, sb), G)
+                    count += 1
+    assert count == 56          # 14 + 18 + 24 (range 2, 3, 4)
+
+
+def test_cumulative_layer_reordering_breaks_the_code(oracle):
+    """Reordering the layers of a subgraph that an earlier event left with
+    mixed stage bits does not encode G_N: the reason every event is applied to
+    the original graph."""
+    n, N = 3, 8
+    sb1 = oracle.graph_from_event(n, oracle.Event.make(1, 2, 0, [1, 0]))
+    sb2 = sb1.copy()
+    sb2[1], sb2[2] = sb1[2].copy(), sb1[1].copy()   # second event: levels 2..3 of the whole graph, swapped
+    assert not np.array_equal(_graph_matrix(oracle, n, sb2), kron_G(n))
+    sb_orig = oracle.graph_from_event(n, oracle.Event.make(2, 2, 0, [1, 0]))
+    assert np.array_equal(_graph_matrix(oracle, n, sb_orig), kron_G(n))
+
+
+def test_graph_encode_rejects_inconsistent_pairing(oracle):
+    sb = oracle.graph_from_event(3)
+    sb[0, 0] = 1   # index 0 pairs with 2 but 2 pairs with 3
+    with pytest.raises(ValueError):
+        oracle.graph_encode(3, sb, np.zeros(8, dtype=np.uint8))
+
+
+def test_fig3_subgraph_counts_and_zeroed_nodes(oracle, golden_dir):
+    rows = [ln.split() for ln in (golden_dir / "fig3_subgraphs.txt").read_text().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    for N, level, rng_, nsub, levels in rows:
+        N, level, rng_, nsub = int(N), int(level), int(rng_), int(nsub)
+        n = N.bit_length() - 1
+        m = level + rng_ - 1
+        assert N >> m == nsub
+        ev = oracle.Event.make(level, rng_, nsub - 1, list(range(rng_))[::-1])
+        assert oracle.n_zero(ev) == (rng_ - 1) * (1 << m)
+        assert [int(v) for v in levels.split(",")] == list(range(level + 1, level + rng_))
+
+
+def test_eq2_reset_increments_table1(oracle, golden_dir):
+    rows = [ln.split("#")[0].split() for ln in (golden_dir / "table1_reset.txt").read_text().splitlines()
+            if ln.strip() and not ln.startswith("#")]
+    for N, n, level, rng_, D, N_min, nz, inc in (map(int, r) for r in rows):
+        ev = oracle.Event.make(level, rng_, 0, list(range(rng_)))
+        assert oracle.n_zero(ev) == nz
+        s = oracle.Sched(mode=1, N_min=N_min, D=D)
+        assert oracle.reset_increment(s, ev) == inc
+    # the full-graph case of the D heuristic: N_zero = N (n - 1)
+    assert oracle.n_zero(oracle.Event.make(1, 10, 0, list(range(10)))) == 1024 * 9
+
+
+def test_zeroing_touches_exactly_the_interior_nodes(oracle):
+    """resetVariableNodes after a switch: L and R of the interior levels of the
+    chosen subgraph become 0, every other message is unchanged."""
+    n, N = 5, 32
+    _, fr = oracle.construct(N, 16)
+    rng = np.random.default_rng(3)
+    llr = rng.normal(2.0, 2.0, N)
+    ev = oracle.Event.make(2, 3, 1, [2, 0, 1])        # levels 2..4, subgraph 1 of 2 (odd indices)
+    sw = oracle.Sched(mode=1, T0=1, N_min=100, stop_kind=0, alpha=0.9375)
+    plain = oracle.Sched(mode=0, stop_kind=0, alpha=0.9375)
+    a = oracle.decode(fr, 0, 0, llr, sw, 1, events=[ev], dump=True, dtype=np.float64).dump[0]
+    b = oracle.decode(fr, 0, 0, llr, plain, 1, dump=True, dtype=np.float64).dump[0]
+    mask = np.zeros((n + 1, N), dtype=bool)
+    for lev in (3, 4):
+        mask[lev - 1, 1::2] = True
+    for side in (0, 1):
+        assert np.all(a[side][mask] == 0)
+        assert np.array_equal(a[side][~mask], b[side][~mask])
+    assert mask.sum() == oracle.n_zero(ev)
+
+
+# --------------------------------------------------------------- event draws (Sec. III)
+def test_event_draw_bounds_and_uniformity(oracle):
+    n = 10
+    s = oracle.Sched(mode=1, P_range=6, P_level=7, seed=11)
+    counts = {}
+    for frame in range(2000):
+        for k in range(5):
+            ev = oracle.draw_event(n, s, frame, k)
+            assert 2 <= ev.range <= 6
+            assert 1 <= ev.level <= min(7, n - ev.range + 1)
+            m = ev.level + ev.range - 1
+            assert 0 <= ev.block < (1 << n) >> m
+            order = list(ev.order[: ev.range])
+            assert sorted(order) == list(range(ev.range)) and order != list(range(ev.range))
+            counts[ev.range] = counts.get(ev.range, 0) + 1
+    # rho_range uniform on {2..P_range}: 10000 draws over 5 values
+    assert all(abs(c - 2000) < 250 for c in counts.values()) and len(counts) == 5
+
+
+def test_event_draw_fixed_range_and_full(oracle):
+    s = oracle.Sched(mode=1, rho_range_fixed=4, P_level=9, seed=3)
+    levels = set()
+    for frame in range(500):
+        ev = oracle.draw_event(10, s, frame, 0)
+        assert ev.range == 4 and 1 <= ev.level <= 7
+        levels.add(ev.level)
+    assert levels == set(range(1, 8))           # min(x, n - rho_range + 1), x on 1..9
+    f = oracle.Sched(mode=2, seed=3)
+    ev = oracle.draw_event(10, f, 5, 2)
+    assert (ev.level, ev.range, ev.block) == (1, 10, 0)
+
+
+def test_splitmix64_published_first_output(oracle):
+    # SplitMix64 seeded with 0 outputs 0xE220A8397B1DCDAF first (public reference generator).
+    assert oracle.splitmix(0) == 0xE220A8397B1DCDAF
+    assert oracle.hash64(1, 2, 3, 4) == oracle.splitmix(oracle.splitmix(oracle.splitmix(oracle.splitmix(1) ^ 2) ^ 3) ^ 4)
+
+
+# --------------------------------------------------------------- Sec. II-A construction
+def _bec_sc_erasure(N, eps):
+    """Exact SC erasure probabilities of u_i over BEC(eps): u_i is decided when
+    e_i lies in the GF(2) span of the observed columns of G and e_0..e_{i-1}."""
+    n = N.bit_length() - 1
+    G = kron_G(n)
+    cols = [int("".join(str(int(G[j, k])) for j in range(N)), 2) for k in range(N)]   # column k as a u-functional
+    unit = [1 << (N - 1 - i) for i in range(N)]
+
+    def rank(vecs):
+        basis = []
+        for v in vecs:
+            for b in basis:
+                v = min(v, v ^ b)
+            if v:
+                basis.append(v)
+        return len(basis)
+
+    p = np.zeros(N)
+    for pat in range(1 << N):
+        erased = [k for k in range(N) if (pat >> k) & 1]
+        w = eps ** len(erased) * (1 - eps) ** (N - len(erased))
+        obs = [cols[k] for k in range(N) if not (pat >> k) & 1]
+        for i in range(N):
+            known = obs + unit[:i]
+            if rank(known + [unit[i]]) != rank(known):
+                p[i] += w
+    return p
+
+
+@pytest.mark.parametrize("N", [4, 8])
+def test_construction_equals_exact_bec_sc_erasure(oracle, N):
+    K = N // 2
+    lz, fr = oracle.construct(N, K, 0.0)
+    eps = float(np.exp(-(K / N)))                   # z0 = exp(-R Eb/N0) at 0 dB
+    assert np.allclose(np.exp(lz), _bec_sc_erasure(N, eps), rtol=1e-12, atol=0)
+
+
+def test_construction_n4_prefers_index_2_over_1(oracle):
+    _, fr = oracle.construct(4, 2)
+    assert list(np.nonzero(fr == 0)[0]) == [2, 3]
+    _, fr = oracle.construct(8, 4)
+    assert list(np.nonzero(fr == 0)[0]) == [3, 5, 6, 7]
+
+
+@pytest.mark.parametrize("N,K,db", [(64, 32, 0.0), (256, 128, 0.0), (512, 256, 1.0), (128, 96, -1.0)])
+def test_construction_log_domain_vs_high_precision_linear(oracle, N, K, db):
+    # 1 - z reaches ~1e-210 at N = 512: 400 digits keep the linear domain exact enough
+    mp.mp.dps = 400
+    z = [mp.e ** (-(mp.mpf(K) / N) * mp.power(10, mp.mpf(db) / 10))]
+    while len(z) < N:
+        nz = []
+        for v in z:
+            nz += [2 * v - v * v, v * v]
+        z = nz
+    lz, fr = oracle.construct(N, K, db)
+    ref = np.array([float(mp.log(v)) for v in z])
+    assert np.allclose(lz, ref, rtol=1e-10, atol=1e-300)
+    order = sorted(range(N), key=lambda i: (-z[i], i))
+    want = np.zeros(N, dtype=np.uint8)
+    want[order[: N - K]] = 1
+    assert np.array_equal(fr, want)
+
+
+# --------------------------------------------------------------- CRC (Sec. IV)
+def _gf2_mod(bits, r, poly):
+    g = poly | (1 << r)
+    v = int("".join(str(int(b)) for b in bits), 2) if len(bits) else 0
+    while v.bit_length() > r:
+        v ^= g << (v.bit_length() - 1 - r)
+    return v
+
+
+def test_crc_published_check_value(oracle, golden_dir):
+    msg = np.unpackbits(np.frombuffer(b"123456789", dtype=np.uint8))
+    for ln in (golden_dir / "crc_check_values.txt").read_text().splitlines():
+        if ln.strip() and not ln.startswith("#"):
+            r, poly, check = ln.split()
+            assert oracle.crc_compute(msg, int(r), int(poly, 16)) == int(check, 16)
+
+
+@pytest.mark.parametrize("r,poly", [(8, POLY8), (24, POLY24), (24, POLY24 & 0xFFFFFF)])
+def test_crc_is_polynomial_division(oracle, r, poly):
+    rng = np.random.default_rng(r)
+    for L in (0, 1, 7, 30, 488, 1000):
+        bits = rng.integers(0, 2, L).astype(np.uint8)
+        assert oracle.crc_residue(bits, r, poly) == _gf2_mod(bits, r, poly & ((1 << r) - 1))
+        aug = np.concatenate([bits, np.zeros(r, dtype=np.uint8)])
+        assert oracle.crc_compute(bits, r, poly) == _gf2_mod(aug, r, poly & ((1 << r) - 1))
+
+
+@pytest.mark.parametrize("r,poly", [(8, POLY8), (24, POLY24)])
+def test_crc_codewords_have_zero_residue_and_residue_is_linear(oracle, r, poly):
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        p = rng.integers(0, 2, 200).astype(np.uint8)
+        assert oracle.crc_residue(oracle.crc_bits(p, r, poly), r, poly) == 0
+        a, b = rng.integers(0, 2, (2, 224)).astype(np.uint8)
+        assert oracle.crc_residue(a ^ b, r, poly) == oracle.crc_residue(a, r, poly) ^ oracle.crc_residue(b, r, poly)
+
+
+# --------------------------------------------------------------- f (Sec. II-B)
+def test_min_sum_closed_forms(oracle):
+    for dt in (np.float64, np.float32):
+        for alpha in (1.0, 0.9375):
+            assert oracle.f(0.0, 3.5, alpha, 0, dt) == 0.0
+            assert oracle.f(np.inf, -2.0, alpha, 0, dt) == dt(alpha) * dt(-2.0)
+            assert oracle.f(np.inf, np.inf, alpha, 0, dt) == np.inf
+            assert oracle.f(-3.0, 2.0, alpha, 0, dt) == -(dt(alpha) * dt(2.0))
+            assert oracle.f(-3.0, -2.5, alpha, 0, dt) == dt(alpha) * dt(2.5)
+            assert oracle.f(1.25, -7.0, alpha, 0, dt) == oracle.f(-7.0, 1.25, alpha, 0, dt)
+
+
+def test_box_plus_matches_tanh_rule(oracle):
+    mp.mp.dps = 40
+    rng = np.random.default_rng(9)
+    for a, b in rng.normal(0, 6, (300, 2)):
+        ref = float(2 * mp.atanh(mp.tanh(mp.mpf(a) / 2) * mp.tanh(mp.mpf(b) / 2)))
+        assert abs(oracle.f(a, b, 1.0, 1) - ref) <= 1e-12 * max(1.0, abs(ref))
+    assert oracle.f(np.inf, -1.75, 1.0, 1) == -1.75
+    assert oracle.f(0.0, 5.0, 1.0, 1) == 0.0
+
+
+# --------------------------------------------------------------- BP closed forms (Sec. II-B)
+def _superset_reduce(vals, alpha, n, exact):
+    N = 1 << n
+    out = np.zeros(N)
+    for i in range(N):
+        sup = [vals[j] for j in range(N) if (j & i) == i]
+        if exact:
+            t = mp.mpf(1)
+            for v in sup:
+                t *= mp.tanh(mp.mpf(v) / 2)
+            out[i] = float(2 * mp.atanh(t))
+        else:
+            zeros = n - bin(i).count("1")
+            sgn = np.prod(np.sign(sup))
+            out[i] = sgn * alpha ** zeros * np.min(np.abs(sup))
+    return out
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_first_L_sweep_without_priors_is_superset_reduction(oracle, exact):
+    """With all R zero, L[n+1][j] after one sweep combines the channel LLRs of
+    every x_i with i a bitwise superset of j (u_j is their XOR, Eq. 1)."""
+    mp.mp.dps = 40
+    n, N, alpha = 5, 32, 0.9375
+    rng = np.random.default_rng(4)
+    L = np.zeros((n + 1, N))
+    R = np.zeros((n + 1, N))
+    L[0] = rng.normal(1.0, 2.0, N)
+    oracle.bp_iteration(n, oracle.graph_from_event(n), L, R, 1.0 if exact else alpha, 1 if exact else 0)
+    ref = _superset_reduce(L[0], alpha, n, exact)
+    assert np.allclose(L[n], ref, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("exact", [False, True])
+def test_R_sweep_without_channel_is_superset_reduction(oracle, exact):
+    mp.mp.dps = 40
+    n, N, alpha = 5, 32, 0.9375
+    rng = np.random.default_rng(6)
+    L = np.zeros((n + 1, N))
+    R = np.zeros((n + 1, N))
+    R[n] = rng.normal(0.5, 3.0, N)
+    oracle.bp_iteration(n, oracle.graph_from_event(n), L, R, 1.0 if exact else alpha, 1 if exact else 0)
+    assert np.all(L[1:] == 0)
+    assert np.allclose(R[0], _superset_reduce(R[n], alpha, n, exact), rtol=1e-9, atol=1e-12)
+
+
+def test_n2_single_pe_is_map(oracle):
+    """N = 2 is a tree: one iteration gives the MAP LLRs.  With u1 frozen,
+    u0 = x0 and x1 = 0 is known; with u0 frozen, x0 = x1 = u1."""
+    l0, l1 = 0.7, -2.3
+    sb = oracle.graph_from_event(1)
+    L = np.array([[l0, l1], [0.0, 0.0]])
+    R = np.array([[0.0, 0.0], [0.0, np.inf]])
+    oracle.bp_iteration(1, sb, L, R, 1.0, 0)
+    assert L[1, 0] == l0 and L[1, 1] == l1 and R[0, 0] == 0.0 and R[0, 1] == np.inf
+    L = np.array([[l0, l1], [0.0, 0.0]])
+    R = np.array([[0.0, 0.0], [np.inf, 0.0]])
+    oracle.bp_iteration(1, sb, L, R, 1.0, 0)
+    assert L[1, 1] == l0 + l1 and R[0, 0] == l1 and R[0, 1] == l0
+
+
+def test_repetition_code_reaches_map_sum(oracle):
+    """Only u_{N-1} free: x = u_{N-1} * ones, MAP LLR = sum of the channel LLRs;
+    exact box-plus BP reaches it (uses the previous iteration's R planes)."""
+    N, n = 64, 6
+    fr = np.ones(N, dtype=np.uint8)
+    fr[-1] = 0
+    llr = np.random.default_rng(1).normal(1.0, 1.0, N)
+    res = oracle.decode(fr, 0, 0, llr, oracle.Sched(mode=0, stop_kind=0, fkind=1, alpha=1.0), 2 * n,
+                        dump=True, dtype=np.float64)
+    assert abs(res.dump[-1, 0, n, N - 1] - llr.sum()) < 1e-9
+
+
+def test_single_parity_check_extrinsic(oracle):
+    """Only u_0 frozen: the code is the even-weight code; R[1] holds the
+    extrinsic LLR of each x_i, the box-plus of all other channel LLRs."""
+    N, n = 32, 5
+    fr = np.zeros(N, dtype=np.uint8)
+    fr[0] = 1
+    llr = np.random.default_rng(2).normal(1.5, 1.0, N)
+    res = oracle.decode(fr, 0, 0, llr, oracle.Sched(mode=0, stop_kind=0, fkind=1, alpha=1.0), 3,
+                        dump=True, dtype=np.float64)
+    ext = np.array([2 * np.arctanh(np.prod(np.tanh(np.delete(llr, i) / 2))) for i in range(N)])
+    assert np.allclose(res.dump[-1, 1, 0], ext, rtol=1e-10, atol=1e-12)
+
+
+# --------------------------------------------------------------- Algorithm 1 invariants
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_noiseless_frames_decode_exactly(oracle, mode, dtype):
+    N, K, r = 128, 64, 8
+    _, fr = oracle.construct(N, K)
+    rng = np.random.default_rng(mode)
+    s = oracle.Sched(mode=mode, P_range=4, P_level=6, N_min=3, D=0, T0=2, it_reset_full=3, q_max=0,
+                     stop_from=1, stop_kind=1, seed=9)
+    for _ in range(5):
+        pay = rng.integers(0, 2, K - r).astype(np.uint8)
+        x = oracle.encode_frames(pay[None], fr, r, POLY8)[0]
+        llr = (1 - 2 * x.astype(np.float64)) * 12.0
+        res = oracle.decode(fr, r, POLY8, llr, s, 40, dtype=dtype)
+        assert res.iters == 1 and res.crc_ok == 1
+        assert np.array_equal(oracle.info_bits(res.uhat, fr)[: K - r], pay)
+        # keep iterating through many switches: every permuted graph keeps the codeword a fixed point
+        s2 = oracle.Sched(**{**s.__dict__, "stop_kind": 0})
+        res = oracle.decode(fr, r, POLY8, llr, s2, 40, dtype=dtype)
+        assert res.iters == 40 and res.crc_ok == 1
+        assert np.array_equal(oracle.info_bits(res.uhat, fr)[: K - r], pay)
+
+
+def test_g_matrix_stop_on_noiseless(oracle):
+    N, K = 64, 32
+    _, fr = oracle.construct(N, K)
+    pay = np.random.default_rng(0).integers(0, 2, K).astype(np.uint8)
+    x = oracle.encode_frames(pay[None], fr, 0, 0)[0]
+    llr = (1 - 2 * x.astype(np.float32)) * 8.0
+    res = oracle.decode(fr, 0, 0, llr, oracle.Sched(mode=0, stop_kind=2), 20)
+    assert res.iters == 1 and np.array_equal(oracle.info_bits(res.uhat, fr), pay)
+
+
+def test_stop_from_delays_the_stop(oracle):
+    N, K = 64, 32
+    _, fr = oracle.construct(N, K)
+    llr = np.full(N, 5.0, dtype=np.float32)
+    res = oracle.decode(fr, 8, POLY8, llr, oracle.Sched(mode=0, stop_kind=1, stop_from=4), 20)
+    assert res.iters == 4 and res.crc_ok == 1
+
+
+def test_zero_iterations_decides_all_zero(oracle):
+    _, fr = oracle.construct(32, 16)
+    res = oracle.decode(fr, 8, POLY8, -np.ones(32, dtype=np.float32), oracle.Sched(), 0)
+    assert res.iters == 0 and not res.uhat.any() and res.crc_ok == 1
+
+
+def test_fp32_and_fp64_agree_on_noisy_frames(oracle):
+    """FP32 vs FP64 oracle at 3 dB: every frame that either precision decodes
+    correctly gets identical decisions in both; frames that fail may wander
+    apart (rounding steers a non-converging trajectory)."""
+    N, K, r = 256, 128, 8
+    _, fr = oracle.construct(N, K)
+    B = 1500
+    pay = inputs.payload_numpy(21, B, K - r)
+    x = oracle.encode_frames(pay, fr, r, POLY8)
+    llr = inputs.bpsk_awgn_llr(x, inputs.noise_numpy(21, B, N), inputs.sigma2_of(3.0, K, r, N))
+    s = oracle.Sched(mode=1, rho_range_fixed=3, P_level=7, N_min=10, D=0, T0=10, stop_kind=1, seed=3)
+    u32, it32, _ = oracle.decode_batch(fr, r, POLY8, llr, s, 50, dtype=np.float32)
+    u64, it64, _ = oracle.decode_batch(fr, r, POLY8, llr.astype(np.float64), s, 50, dtype=np.float64)
+    same = np.all(u32 == u64, axis=1)
+    ok32 = np.all(oracle.info_bits(u32, fr)[:, : K - r] == pay, axis=1)
+    ok64 = np.all(oracle.info_bits(u64, fr)[:, : K - r] == pay, axis=1)
+    assert np.all(same[ok32 | ok64])
+    assert np.mean(it32[ok32 | ok64] == it64[ok32 | ok64]) >= 0.99
+    assert same.mean() >= 0.99
+    assert ok32.mean() > 0.9        # 3 dB, N = 256 rate 1/2: BP decodes the vast majority
