@@ -1,0 +1,358 @@
+"""Throughput of the GB300 PP-BP polar decoder (arXiv 1911.08868).
+
+Workload (one step): 1,000,000 synthetic BPSK/AWGN frames of the N = 1024,
+K = 512 polar code with CRC-24 (0x1B2B117), Bhattacharyya construction at
+0 dB, decoded by partially permuted multi-trellis BP with subgraphs of s = 4
+stages switched every T = 10 iterations (P_level = n - 1), at most 300
+iterations, scaled min-sum alpha = 0.9375, CRC stop, Eb/N0 = 3.0 dB.  The
+LLRs (4.1 GB per step) are resident in HBM and larger than L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  `value` is decoded information (payload) Gbit/s over
+all ranks, timed with CUDA events around the decoder launches; `e2e` is the
+same metric through the host-buffer API (pinned host LLRs copied in, results
+copied out, every step).  `--impl reference` times the CPU oracle on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "decoded info Gbit/s @N=1024 R=0.5 PPMT-BP, FER-matched; WBP fwd+bwd steps/s"
+N, K, R_CRC, POLY = 1024, 512, 24, 0x1B2B117
+EBN0 = 3.0
+MAX_ITERS = 300
+FRAMES = 1_000_000
+SCHED = dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, D=0, T0=10, stop_from=1, stop_kind=1,
+             alpha=0.9375, seed=3)
+WORKLOAD = "PP-BP N=1024 K=512 CRC-24, s=4 T=10, max 300 it, min-sum a=0.9375, BPSK/AWGN Eb/N0=3.0 dB"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="wall-time budget of the CPU oracle sample")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_1911_08868_gb300" / "csrc").glob("bp_*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    return json.loads(p.read_text()) if p.exists() else None
+
+
+def profiled_traffic(sha: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
+    p = ROOT / "profiles" / "bp_decode_n1024_traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    return d.get("dram_bytes_per_launch") if d.get("kernel_sha") == sha else None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = []
+        for ln in (self.out or "").splitlines():
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append(parts)
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_oracle(frames_budget_s: float, seed: int = 97):
+    """The oracle as it stands (FP32, OpenMP over frames) on host cores, on
+    chunks of the workload until the wall-time budget is used."""
+    import numpy as np
+
+    import oracle as O
+    from paper_1911_08868_gb300 import inputs
+
+    _, fr = O.construct(N, K)
+    s = O.Sched(**{**SCHED, "alpha": 0.9375})
+    threads = O.max_threads()
+    chunk = max(256, 64 * threads)
+    done = bits = iters_sum = errs = 0
+    elapsed = 0.0
+    c = 0
+    while elapsed < frames_budget_s or done == 0:
+        pay = inputs.payload_numpy(seed + c, chunk, K - R_CRC)
+        x = O.encode_frames(pay, fr, R_CRC, POLY)
+        llr = inputs.bpsk_awgn_llr(x, inputs.noise_numpy(seed + c, chunk, N), inputs.sigma2_of(EBN0, K, R_CRC, N))
+        s.frame_base = done
+        t0 = time.perf_counter()
+        u, it, ok = O.decode_batch(fr, R_CRC, POLY, llr, s, MAX_ITERS, nthreads=threads)
+        elapsed += time.perf_counter() - t0
+        got = O.info_bits(u, fr)[:, : K - R_CRC]
+        errs += int((got != pay).any(axis=1).sum())
+        iters_sum += int(it.sum())
+        done += chunk
+        bits += chunk * (K - R_CRC)
+        c += 1
+    return {"gbps": bits / elapsed / 1e9, "frames": done, "seconds": elapsed, "cores": threads,
+            "fer": errs / done, "errors": errs, "mean_iters": iters_sum / done}
+
+
+def wilson(k: int, n: int, z: float = 1.96):
+    if n == 0:
+        return [0.0, 1.0]
+    p = k / n
+    d = 1 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    steps, warm = args.steps, args.warmup
+    per = max(args.cpu_seconds / max(steps + warm, 1), 0.5)
+    for _ in range(warm):
+        cpu_oracle(per * 0.25, seed=1000)
+    runs = [cpu_oracle(per, seed=2000 + i) for i in range(steps)]
+    frames = sum(r["frames"] for r in runs)
+    secs = sum(r["seconds"] for r in runs)
+    gbps = frames * (K - R_CRC) / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gbps, "unit": "Gbit/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": warm, "ms_per_step": secs / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": runs[0]["frames"], "note": "bounded sample per step"},
+        "cpu_baseline": {"value": gbps, "unit": "Gbit/s", "cores": runs[0]["cores"], "kind": "oracle",
+                         "sample": f"{frames} frames over {steps} steps, ~{per:.1f} s each"},
+        "e2e": {"value": gbps, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "fer": sum(r["errors"] for r in runs) / frames,
+        "mean_iters": sum(r["mean_iters"] * r["frames"] for r in runs) / frames,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1911_08868_gb300 import _build
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        _build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1911_08868_gb300 import inputs, pcbp
+
+    B = args.frames
+    code = pcbp.pc_construct(N, K, R_CRC, POLY)
+    sch = pcbp.sched(**SCHED, frame_base=rank * B)
+    gen = torch.Generator(device=dev).manual_seed(1234 + rank)
+    pay = inputs.payload_torch(gen, B, K - R_CRC, dev)
+    x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+    pcbp.pc_encode(code, pay, x)
+    llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(EBN0, K, R_CRC, N)).contiguous()
+    del x
+    torch.cuda.synchronize()
+    dec = pcbp.Decoder(code, sch, MAX_ITERS, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        dec(llr)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    t_all0 = torch.cuda.Event(enable_timing=True)
+    t_all1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        torch.cuda.synchronize()
+        t_all0.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            dec(llr)
+            ends[i].record(stream)
+        t_all1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = t_all0.elapsed_time(t_all1)
+    launch_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+
+    # outcome of the decode (identical every step)
+    iters = dec.iters.to(torch.int64)
+    ok = dec.crc_ok.to(torch.int64)
+    got = pcbp.unpack_bits(dec.bits, K)[:, : K - R_CRC]
+    frame_err = (got != pay).any(dim=1)
+    errors = int(frame_err.sum().item())
+    mean_iters = float(iters.float().mean().item())
+    half_sweeps = int((2 * iters - ok).sum().item())   # a CRC stop skips that iteration's R sweep
+    info_bits = B * (K - R_CRC)
+    value = world * info_bits * args.steps / (total_ms / 1e3) / 1e9
+
+    # roofline: plain-ALU bound.  Per PE and half sweep: 2 f (min, scale,
+    # sign) + 2 adds = 8 lane-ops; a half sweep has n N / 2 PEs.
+    n = N.bit_length() - 1
+    lane_ops = half_sweeps * (n * N // 2) * 8
+    mean_launch_s = statistics.mean(launch_ms) / 1e3
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_mhz_max = (peaks or {}).get("sm_max_mhz", 2070.0)
+    peak_ops = props.multi_processor_count * 128 * sm_mhz_max * 1e6
+    achieved = lane_ops / mean_launch_s
+    sha = kernel_sha()
+    roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
+            "frac": achieved / peak_ops, "traffic": profiled_traffic(sha),
+            "algorithmic_bytes": B * N * 4 + B * (4 * math.ceil(K / 32) + 5),
+            "hbm_gbs": (B * N * 4 + B * (4 * math.ceil(K / 32) + 5)) / mean_launch_s / 1e9,
+            "peak_source": ("issue rate 128 lanes/clk/SM x %d SMs x %.0f MHz (MEASURED_PEAKS sm_max_mhz)"
+                            % (props.multi_processor_count, sm_mhz_max)),
+            "kernel_sha": sha}
+
+    clocks = clk.summary()
+    line = None
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": B, "N": N, "K": K, "crc": R_CRC,
+                       "ebn0_db": EBN0, "max_iters": MAX_ITERS,
+                       "l2": "inputs larger than L2 (%.1f GB of LLRs per step)" % (B * N * 4 / 1e9),
+                       "parallelism": f"frame shards x{world}"},
+            "frames_per_s": world * B * args.steps / (total_ms / 1e3),
+            "mean_iters": mean_iters, "fer": errors / B, "fer_ci95": wilson(errors, B),
+            "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
+        }
+
+    if not args.no_e2e:
+        hdec = pcbp.HostDecoder(code, sch, MAX_ITERS, dev)
+        h_llr = torch.empty((B, N), dtype=torch.float32, pin_memory=True)
+        h_llr.copy_(llr)
+        del llr
+        torch.cuda.empty_cache()
+        hdec(h_llr)
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e_steps = max(1, min(args.steps, 5))
+        for _ in range(e_steps):
+            hb, hi, ho = hdec(h_llr)
+        el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([el], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            el = float(t.item())
+        if rank == 0:
+            same = bool(torch.equal(hi, dec.iters.cpu()))
+            line["e2e"] = {"value": world * info_bits * e_steps / el / 1e9, "unit": "Gbit/s",
+                           "h2d_bytes_per_step": B * N * 4,
+                           "d2h_bytes_per_step": B * (4 * math.ceil(K / 32) + 4 + 1), "steps": e_steps,
+                           "chunks": hdec.chunks, "matches_device_run": same}
+
+    if rank == 0 and not args.no_cpu:
+        cb = cpu_oracle(args.cpu_seconds)
+        line["cpu_baseline"] = {"value": cb["gbps"], "unit": "Gbit/s", "cores": cb["cores"], "kind": "oracle",
+                                "sample": f"{cb['frames']} frames of the same workload (fresh seeds), "
+                                          f"{cb['seconds']:.1f} s",
+                                "fer": cb["fer"], "fer_ci95": wilson(cb["errors"], cb["frames"]),
+                                "mean_iters": cb["mean_iters"]}
+        lo, hi_ = line["cpu_baseline"]["fer_ci95"]
+        line["fer_matched"] = bool(lo <= line["fer"] <= hi_ or line["fer_ci95"][0] <= cb["fer"] <= line["fer_ci95"][1])
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

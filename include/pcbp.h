@@ -1,0 +1,161 @@
+/*
+ * pcbp — GB300 (sm_103a) decoder library for polar codes with partially
+ * permuted multi-trellis belief propagation (PP-BP), after Ranasinghe,
+ * Rajatheva and Latva-aho, "Partially Permuted Multi-Trellis Belief
+ * Propagation for Polar Codes" (arXiv 1911.08868).
+ *
+ * C ABI.  Conventions shared by every call:
+ *   - Every call returns an int status: PC_OK (0) or a negative PC_E* code.
+ *     Argument errors are detected on the host before anything is enqueued.
+ *     PC_ECUDA means a CUDA runtime call failed (launch error, bad device
+ *     pointer detected by the runtime); the stream may hold partial work.
+ *   - All buffers are owned by the caller.  "d_" pointers are device
+ *     pointers, "h_" pointers and struct pointers are host pointers.  Device
+ *     calls never allocate device memory: scratch space is caller-provided
+ *     and sized by the matching *_workspace_size call.
+ *   - Device calls are asynchronous on the caller's stream (a cudaStream_t
+ *     passed as void*, NULL = legacy default stream); outputs are valid
+ *     once the stream has reached that point.  Calls that share a workspace
+ *     must be ordered on one stream.
+ *   - pc_code is an immutable value: it may be shared across streams and
+ *     threads.
+ *   - Bits are one per byte (0/1) on input; decoded information bits are
+ *     packed 32 per uint32_t word, bit k of the information vector in word
+ *     k/32 at bit position k%32.
+ *
+ * Supported sizes: N = 2^n with 3 <= n <= 11 (8 .. 2048), 1 <= K <= N,
+ * CRC length 0 .. 32 (less than K).
+ */
+#ifndef PCBP_H
+#define PCBP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PC_OK 0
+#define PC_EINVAL (-1)      /* an argument is out of range or a pointer is NULL */
+#define PC_ENOMEM (-2)      /* a caller buffer is too small */
+#define PC_ECUDA (-3)       /* a CUDA runtime call failed */
+#define PC_ETIMEOUT (-4)    /* a bounded device wait gave up */
+#define PC_EUNSUPPORTED (-5)/* size or mode not built into this library */
+
+#define PC_NMAX 2048
+#define PC_MAX_EVENTS 32
+
+/* A polar code (Sec. II-A): length N = 2^n, K information positions
+ * (including the crc_len CRC bits), frozen set, CRC generator.
+ *   frozen_mask: bit j%32 of word j/32 is 1 when position j is frozen.
+ *   info_idx[0..K-1]: the information positions in ascending order; the
+ *     information vector a = payload (K - crc_len bits) || CRC (crc_len bits)
+ *     goes to these positions in order.
+ *   crc_poly: generator including its x^crc_len term (bit crc_len set). */
+typedef struct {
+    int32_t N, n, K, crc_len;
+    uint64_t crc_poly;
+    uint32_t frozen_mask[PC_NMAX / 32];
+    int32_t info_idx[PC_NMAX];
+} pc_code;
+
+/* Decoder schedule (Algorithm 1 and Table I).
+ *   mode: 0 plain BP (one trellis), 1 PP-BP (partial permutations),
+ *         2 FP-BP (full permutations, Sec. II-D).
+ *   PP-BP: rho_range is uniform on {2..P_range} unless rho_range_fixed > 0;
+ *     rho_level = min(x, n - rho_range + 1) with x uniform on {1..P_level};
+ *     first switch after T0 iterations, then after max(N_min, floor(N_zero/D))
+ *     (Eq. 2), D == 0 meaning D = infinity.
+ *   FP-BP: a new full stage order every it_reset_full iterations, at most
+ *     q_max - 1 switches (q_max <= 0: unlimited).
+ *   stop_from: first iteration at which the stop test is applied (Sec. IV
+ *     skips "the first few" iterations); stop_kind bit 0 = CRC residue zero,
+ *     bit 1 = G-matrix test (u G_N equals the hard decisions of L1 + R1);
+ *     0 = never stop early.
+ *   fkind: 0 scaled min-sum f = alpha * sign * sign * min (alpha = 1 is the
+ *     paper's unscaled min-sum), 1 exact box-plus (alpha unused).
+ *   seed, frame_base: frame b of a call draws its events from the counter
+ *     generator keyed by (seed, frame_base + b, event index, draw index). */
+typedef struct {
+    int32_t mode, P_range, P_level, N_min, D, T0, rho_range_fixed;
+    int32_t q_max, it_reset_full, stop_from, stop_kind, fkind;
+    float alpha;
+    int32_t reserved;
+    uint64_t seed;
+    uint64_t frame_base;
+} pc_sched;
+
+/* One explicit permutation event (Algorithm 1, partialPermute).  The
+ * original factor graph is Arikan's graph of x = u F^{(x)n}: stage l (1..n,
+ * counted from the channel) pairs positions that differ in bit n-l.  With
+ * m = level+range-1, stages 1..m split the positions into N/2^m subgraphs of
+ * positions that share their n-m low bits; `block` (0 .. N/2^m - 1) is that
+ * low-bit value.  Inside the subgraph, stage level+i takes the bit that stage
+ * level+order[i] has in the original graph; order[0..range-1] is a
+ * permutation of 0..range-1. */
+typedef struct {
+    int32_t level, range;
+    int64_t block;
+    int32_t order[16];
+} pc_event;
+
+/* Code construction by Bhattacharyya bounds at design Eb/N0 (Sec. II-A):
+ * z0 = exp(-(K/N) * 10^(design_ebn0_db/10)), worked in FP64 log domain; the
+ * N-K positions with the largest bound are frozen (ties freeze the lower
+ * index).  crc_poly may omit its x^crc_len term.  Host only. */
+int pc_construct(int32_t N, int32_t K, int32_t crc_len, uint64_t crc_poly,
+                 double design_ebn0_db, pc_code* out);
+
+/* Encoder (Eq. 1): for each of B frames, a = payload || CRC(payload)
+ * (MSB-first polynomial division, zero initial value, no reflection, no
+ * final XOR), u = a on the information positions and 0 elsewhere,
+ * x = u G_N.  d_payload: B x (K - crc_len) bytes; d_x: B x N bytes. */
+int pc_encode(const pc_code* code, const uint8_t* d_payload, uint8_t* d_x,
+              int64_t B, void* stream);
+
+/* Bytes of device workspace bp_decode / bp_decode_trace need for B frames
+ * (a frame counter; 256-byte aligned start required). */
+int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes);
+
+/* PP-BP decoder, Algorithm 1, for B frames.
+ *   d_llr: B x N float channel LLRs (positive favours bit 0), 16-byte
+ *     aligned.  Row b is frame b.
+ *   max_iters: N_it,max >= 0.
+ *   d_bits: B x ceil(K/32) words, the decided information vector (payload
+ *     then CRC bits) packed as described above.
+ *   d_iters: B int32, the iteration at which the stop test passed, else
+ *     max_iters.
+ *   d_crc_ok: B bytes, 1 when the decided information vector has zero CRC
+ *     residue (always 1 when crc_len == 0).
+ *   d_workspace: bp_decode_workspace_size bytes, overwritten.
+ * Messages are FP32; every FP32 operation is rounded as written (no fused
+ * multiply-add), so results are reproducible bit for bit. */
+int bp_decode(const pc_code* code, const float* d_llr, const pc_sched* sched,
+              int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
+              uint8_t* d_crc_ok, void* d_workspace, void* stream);
+
+/* bp_decode with every message plane recorded, for verification.
+ *   h_events: when not NULL, the k-th switch applies h_events[k] (for every
+ *     frame) and no switch follows the n_events-th; n_events <=
+ *     PC_MAX_EVENTS.  When NULL, events come from the counter generator as
+ *     in bp_decode.
+ *   d_dump: B x max_iters x 2 x (n+1) x N floats; after iteration i the
+ *     block [b][i-1] holds the L planes of levels 1..n+1 followed by the R
+ *     planes of levels 1..n+1 (after the switch of that iteration, if any).
+ *     Blocks past a frame's last iteration are left untouched.
+ * The final iteration is always completed in full (bp_decode may skip the
+ * last R sweep when only the CRC test stops it; outputs are the same). */
+int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sched,
+                    int32_t max_iters, int64_t B, const pc_event* h_events,
+                    int32_t n_events, float* d_dump, uint32_t* d_bits,
+                    int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
+                    void* stream);
+
+/* Short text for a status code. */
+const char* pc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

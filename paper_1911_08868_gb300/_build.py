@@ -1,0 +1,97 @@
+"""Builds libpcbp.so in-tree with nvcc for sm_103a (no cmake, no setuptools).
+
+The decoder kernels are instantiated once per code length (n = 3..11) from
+``csrc/bp_inst.cu``; those translation units compile in parallel.  Objects go
+to ``_build/`` at the repository root; the library is written next to this
+file.  A rebuild only recompiles objects older than their sources or any
+header.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+from pathlib import Path
+
+PKG = Path(__file__).resolve().parent
+ROOT = PKG.parent
+CSRC = PKG / "csrc"
+INCLUDE = ROOT / "include"
+BUILD = ROOT / "_build"
+LIB = PKG / "libpcbp.so"
+
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+LOGNS = range(3, 12)
+
+
+def _nvcc() -> str:
+    cand = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(cand):
+        raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libpcbp")
+    return cand
+
+
+def _headers() -> list[Path]:
+    return sorted(CSRC.glob("*.h")) + sorted(CSRC.glob("*.cuh")) + sorted(INCLUDE.glob("*.h"))
+
+
+def _stale(obj: Path, src: Path) -> bool:
+    if not obj.exists():
+        return True
+    t = obj.stat().st_mtime
+    return any(p.stat().st_mtime > t for p in [src, *_headers(), Path(__file__)])
+
+
+def _jobs() -> list[tuple[Path, Path, list[str]]]:
+    nvcc = _nvcc()
+    common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
+              f"-I{INCLUDE}", f"-I{CSRC}"]
+    jobs = []
+    for n in LOGNS:
+        obj = BUILD / f"bp_inst_{n}.o"
+        jobs.append((obj, CSRC / "bp_inst.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst.cu"),
+                                                "-o", str(obj)]))
+    for name in ("bp_decode.cu",):
+        obj = BUILD / (Path(name).stem + ".o")
+        jobs.append((obj, CSRC / name, [*common, "-c", str(CSRC / name), "-o", str(obj)]))
+    for name in ("pcbp_host.cpp",):
+        obj = BUILD / (Path(name).stem + ".o")
+        jobs.append((obj, CSRC / name, [*common, "-x", "cu", "-c", str(CSRC / name), "-o", str(obj)]))
+    return jobs
+
+
+def build(verbose: bool = False, force: bool = False) -> Path:
+    """Compile (as needed) and link libpcbp.so; returns its path."""
+    BUILD.mkdir(exist_ok=True)
+    jobs = _jobs()
+    todo = [j for j in jobs if force or _stale(j[0], j[1])]
+
+    def run(job):
+        obj, _, cmd = job
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"compile failed for {obj.name}:\n{res.stdout}\n{res.stderr}")
+        return res.stderr
+
+    if todo:
+        workers = max(1, min(len(todo), os.cpu_count() or 4))
+        with cf.ThreadPoolExecutor(workers) as ex:
+            for msg in ex.map(run, todo):
+                if verbose and msg:
+                    print(msg)
+    objs = [str(j[0]) for j in jobs]
+    if force or todo or not LIB.exists() or any(Path(o).stat().st_mtime > LIB.stat().st_mtime for o in objs):
+        cmd = [_nvcc(), *ARCH, "-shared", "-o", str(LIB), *objs]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+    return LIB
+
+
+if __name__ == "__main__":
+    import sys
+
+    print(build(verbose="-v" in sys.argv, force="-f" in sys.argv))

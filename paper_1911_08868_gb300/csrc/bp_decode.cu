@@ -1,0 +1,273 @@
+// C-ABI entry points of libpcbp: pc_encode, bp_decode, bp_decode_trace.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "bp_launch.h"
+#include "pcbp_internal.h"
+
+namespace pcbp {
+
+namespace {
+
+struct DeviceInfo {
+    int sms = 0;
+    int smem_optin = 0;
+};
+
+int device_info(DeviceInfo* out)
+{
+    static DeviceInfo cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return PC_ECUDA;
+    if (dev < 64 && cache[dev].sms > 0) {
+        *out = cache[dev];
+        return PC_OK;
+    }
+    DeviceInfo d;
+    if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PC_ECUDA;
+    if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return PC_ECUDA;
+    if (dev < 64) cache[dev] = d;
+    *out = d;
+    return PC_OK;
+}
+
+void shape_of(int n, int* T, size_t* slot)
+{
+    switch (n) {
+        case 3: bp_shape_3(T, slot); break;
+        case 4: bp_shape_4(T, slot); break;
+        case 5: bp_shape_5(T, slot); break;
+        case 6: bp_shape_6(T, slot); break;
+        case 7: bp_shape_7(T, slot); break;
+        case 8: bp_shape_8(T, slot); break;
+        case 9: bp_shape_9(T, slot); break;
+        case 10: bp_shape_10(T, slot); break;
+        default: bp_shape_11(T, slot); break;
+    }
+}
+
+int occupancy_of(int n, const LaunchGeom& g, bool trace, int fk)
+{
+    switch (n) {
+        case 3: return bp_occupancy_3(g, trace, fk);
+        case 4: return bp_occupancy_4(g, trace, fk);
+        case 5: return bp_occupancy_5(g, trace, fk);
+        case 6: return bp_occupancy_6(g, trace, fk);
+        case 7: return bp_occupancy_7(g, trace, fk);
+        case 8: return bp_occupancy_8(g, trace, fk);
+        case 9: return bp_occupancy_9(g, trace, fk);
+        case 10: return bp_occupancy_10(g, trace, fk);
+        default: return bp_occupancy_11(g, trace, fk);
+    }
+}
+
+cudaError_t launch_of(int n, const BpParams& P, const LaunchGeom& g, bool trace, int fk, cudaStream_t st)
+{
+    switch (n) {
+        case 3: return bp_launch_3(P, g, trace, fk, st);
+        case 4: return bp_launch_4(P, g, trace, fk, st);
+        case 5: return bp_launch_5(P, g, trace, fk, st);
+        case 6: return bp_launch_6(P, g, trace, fk, st);
+        case 7: return bp_launch_7(P, g, trace, fk, st);
+        case 8: return bp_launch_8(P, g, trace, fk, st);
+        case 9: return bp_launch_9(P, g, trace, fk, st);
+        case 10: return bp_launch_10(P, g, trace, fk, st);
+        default: return bp_launch_11(P, g, trace, fk, st);
+    }
+}
+
+size_t table_bytes(int N, int r, int K)
+{
+    const size_t nw = size_t(N >= 32 ? N / 32 : 1);
+    return (nw * 4 + size_t(r) * nw * 4 + size_t(K) * 2 + 15) & ~size_t(15);
+}
+
+// Slots per CTA: as many frames as shared memory holds, at most 15 (named
+// barriers 1..15) and at most 1024 threads.
+int plan_launch(const pc_code* c, int64_t B, bool trace, int fk, LaunchGeom* g)
+{
+    DeviceInfo di;
+    int rc = device_info(&di);
+    if (rc != PC_OK) return rc;
+    int T = 0;
+    size_t slot = 0;
+    shape_of(c->n, &T, &slot);
+    const size_t tab = table_bytes(c->N, c->crc_len, c->K);
+    if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
+    int slots = int((size_t(di.smem_optin) - tab) / slot);
+    slots = std::min(slots, 15);
+    slots = std::min(slots, 1024 / T);
+    slots = std::max(slots, 1);
+    g->slots = slots;
+    g->smem = tab + size_t(slots) * slot;
+    g->grid = 1;
+    int occ = occupancy_of(c->n, *g, trace, fk);
+    if (occ < 1) return PC_EUNSUPPORTED;
+    const int64_t need = (B + slots - 1) / slots;
+    g->grid = int(std::min<int64_t>(need, int64_t(di.sms) * occ));
+    return PC_OK;
+}
+
+int validate_events(const pc_code* c, const pc_event* ev, int n_ev)
+{
+    if (n_ev < 0 || n_ev > PC_MAX_EVENTS) return PC_EINVAL;
+    if (n_ev > 0 && !ev) return PC_EINVAL;
+    for (int k = 0; k < n_ev; ++k) {
+        const pc_event& e = ev[k];
+        if (e.range < 2 || e.range > 16 || e.level < 1 || e.level + e.range - 1 > c->n) return PC_EINVAL;
+        const int m = e.level + e.range - 1;
+        if (e.block < 0 || e.block >= (int64_t(1) << (c->n - m))) return PC_EINVAL;
+        unsigned seen = 0;
+        for (int i = 0; i < e.range; ++i) {
+            if (e.order[i] < 0 || e.order[i] >= e.range || ((seen >> e.order[i]) & 1u)) return PC_EINVAL;
+            seen |= 1u << e.order[i];
+        }
+    }
+    return PC_OK;
+}
+
+int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters, int64_t B,
+                  bool trace, const pc_event* h_events, int32_t n_events, float* d_dump, uint32_t* d_bits,
+                  int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace, void* stream)
+{
+    int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    rc = validate_sched(code, sched);
+    if (rc != PC_OK) return rc;
+    if (max_iters < 0 || B < 0) return PC_EINVAL;
+    if (B == 0) return PC_OK;
+    if (!d_llr || !d_bits || !d_iters || !d_crc_ok || !d_workspace) return PC_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_llr) & 15u) || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
+        return PC_EINVAL;
+    if (trace) {
+        if (!d_dump) return PC_EINVAL;
+        if (h_events) {
+            rc = validate_events(code, h_events, n_events);
+            if (rc != PC_OK) return rc;
+        }
+    }
+    std::unique_ptr<BpParams> P(new BpParams);
+    std::memset(P.get(), 0, sizeof(BpParams));
+    build_dev_code(code, &P->code);
+    build_dev_sched(sched, &P->sched);
+    if (trace && h_events) {
+        P->sched.n_explicit = n_events;
+        for (int k = 0; k < n_events; ++k) {
+            P->events[k].level = h_events[k].level;
+            P->events[k].range = h_events[k].range;
+            P->events[k].block = h_events[k].block;
+            for (int i = 0; i < 16; ++i) P->events[k].order[i] = (int8_t)(i < h_events[k].range ? h_events[k].order[i] : i);
+        }
+    }
+    P->llr = d_llr;
+    P->bits = d_bits;
+    P->iters = d_iters;
+    P->crc_ok = d_crc_ok;
+    P->counter = reinterpret_cast<unsigned long long*>(d_workspace);
+    P->dump = d_dump;
+    P->B = B;
+    P->max_iters = max_iters;
+
+    LaunchGeom g;
+    rc = plan_launch(code, B, trace, sched->fkind, &g);
+    if (rc != PC_OK) return rc;
+    P->slots = g.slots;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
+    if (launch_of(code->n, *P, g, trace, sched->fkind, st) != cudaSuccess) return PC_ECUDA;
+    return PC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Encoder (Eq. 1): one CTA per frame at a time.  The CRC is the XOR of the
+// per-payload-bit remainders crc_pay[i]; u is built in shared memory and the
+// n butterfly layers x[t] ^= x[t + 2^p] run in place.
+__global__ void __launch_bounds__(256) encode_kernel(const __grid_constant__ EncParams P)
+{
+    extern __shared__ uint8_t su[];
+    __shared__ uint32_t red[8];
+    const int N = P.N, n = P.n, K = P.K, r = P.r, Kp = P.Kp;
+    for (int64_t f = blockIdx.x; f < P.B; f += gridDim.x) {
+        const uint8_t* pay = P.payload + size_t(f) * Kp;
+        uint32_t acc = 0;
+        for (int i = threadIdx.x; i < Kp; i += blockDim.x)
+            if (pay[i] & 1) acc ^= P.crc_pay[i];
+        for (int o = 16; o > 0; o >>= 1) acc ^= __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) su[j] = 0;
+        __syncthreads();
+        uint32_t crc = 0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) crc ^= red[w];
+        for (int k = threadIdx.x; k < K; k += blockDim.x) {
+            const uint8_t bit = k < Kp ? uint8_t(pay[k] & 1) : uint8_t((crc >> (r - 1 - (k - Kp))) & 1u);
+            su[P.info_idx[k]] = bit;
+        }
+        __syncthreads();
+        for (int p = 0; p < n; ++p) {
+            for (int q = threadIdx.x; q < N / 2; q += blockDim.x) {
+                const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
+                su[t] ^= su[t | (1 << p)];
+            }
+            __syncthreads();
+        }
+        uint8_t* x = P.x + size_t(f) * N;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) x[j] = su[j];
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+}  // namespace pcbp
+
+using namespace pcbp;
+
+extern "C" int pc_encode(const pc_code* code, const uint8_t* d_payload, uint8_t* d_x, int64_t B, void* stream)
+{
+    int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    if (B < 0) return PC_EINVAL;
+    if (B == 0) return PC_OK;
+    if (!d_x || (!d_payload && code->K - code->crc_len > 0)) return PC_EINVAL;
+    DeviceInfo di;
+    rc = device_info(&di);
+    if (rc != PC_OK) return rc;
+    std::unique_ptr<EncParams> P(new EncParams);
+    build_enc_params(code, P.get());
+    P->payload = d_payload;
+    P->x = d_x;
+    P->B = B;
+    const int grid = int(std::min<int64_t>(B, int64_t(di.sms) * 8));
+    encode_kernel<<<grid, 256, size_t(code->N), reinterpret_cast<cudaStream_t>(stream)>>>(*P);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
+}
+
+extern "C" int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes)
+{
+    int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    if (B < 0 || !bytes) return PC_EINVAL;
+    *bytes = 256;
+    return PC_OK;
+}
+
+extern "C" int bp_decode(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters,
+                         int64_t B, uint32_t* d_bits, int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
+                         void* stream)
+{
+    return decode_common(code, d_llr, sched, max_iters, B, false, nullptr, 0, nullptr, d_bits, d_iters, d_crc_ok,
+                         d_workspace, stream);
+}
+
+extern "C" int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters,
+                               int64_t B, const pc_event* h_events, int32_t n_events, float* d_dump,
+                               uint32_t* d_bits, int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
+                               void* stream)
+{
+    return decode_common(code, d_llr, sched, max_iters, B, true, h_events, n_events, d_dump, d_bits, d_iters,
+                         d_crc_ok, d_workspace, stream);
+}

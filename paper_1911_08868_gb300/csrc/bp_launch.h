@@ -1,0 +1,34 @@
+// Per-length launch entry points of the decoder kernels (one set per n,
+// defined in bp_inst.cu compiled with PCBP_LOGN = n).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "pcbp_internal.h"
+
+namespace pcbp {
+
+struct LaunchGeom {
+    int grid;
+    int slots;
+    size_t smem;
+};
+
+#define PCBP_DECLARE_LEN(n)                                                                              \
+    void bp_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out);                                \
+    int bp_occupancy_##n(const LaunchGeom& g, bool trace, int fkind);                                    \
+    cudaError_t bp_launch_##n(const BpParams& P, const LaunchGeom& g, bool trace, int fkind, cudaStream_t st);
+
+PCBP_DECLARE_LEN(3)
+PCBP_DECLARE_LEN(4)
+PCBP_DECLARE_LEN(5)
+PCBP_DECLARE_LEN(6)
+PCBP_DECLARE_LEN(7)
+PCBP_DECLARE_LEN(8)
+PCBP_DECLARE_LEN(9)
+PCBP_DECLARE_LEN(10)
+PCBP_DECLARE_LEN(11)
+
+#undef PCBP_DECLARE_LEN
+
+}  // namespace pcbp

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of libpcbp.so (include/pcbp.h): argument marshalling only.
+
+Every function has the C name and forwards device pointers of torch CUDA
+tensors; all decoding work runs in the library's kernels.  Importing this
+module raises ImportError when libpcbp.so is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+from pathlib import Path
+
+_LIB_PATH = Path(__file__).resolve().parent / "libpcbp.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"{_LIB_PATH} is not built; run `python -m paper_1911_08868_gb300._build` "
+                      "(needs nvcc) — the decoder has no CPU fallback")
+_lib = C.CDLL(str(_LIB_PATH))
+
+PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT, PC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+PC_NMAX = 2048
+PC_MAX_EVENTS = 32
+
+EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
+            "pc_status_string")
+
+
+class PcCode(C.Structure):
+    _fields_ = [("N", C.c_int32), ("n", C.c_int32), ("K", C.c_int32), ("crc_len", C.c_int32),
+                ("crc_poly", C.c_uint64), ("frozen_mask", C.c_uint32 * (PC_NMAX // 32)),
+                ("info_idx", C.c_int32 * PC_NMAX)]
+
+    def frozen(self):
+        return [(self.frozen_mask[j >> 5] >> (j & 31)) & 1 for j in range(self.N)]
+
+    def info_positions(self):
+        return [self.info_idx[k] for k in range(self.K)]
+
+
+class PcSched(C.Structure):
+    _fields_ = [(name, C.c_int32) for name in (
+        "mode", "P_range", "P_level", "N_min", "D", "T0", "rho_range_fixed",
+        "q_max", "it_reset_full", "stop_from", "stop_kind", "fkind")] + [
+        ("alpha", C.c_float), ("reserved", C.c_int32), ("seed", C.c_uint64), ("frame_base", C.c_uint64)]
+
+
+class PcEvent(C.Structure):
+    _fields_ = [("level", C.c_int32), ("range", C.c_int32), ("block", C.c_int64), ("order", C.c_int32 * 16)]
+
+
+_vp = C.c_void_p
+_lib.pc_construct.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_double, C.POINTER(PcCode)]
+_lib.pc_encode.argtypes = [C.POINTER(PcCode), _vp, _vp, C.c_int64, _vp]
+_lib.bp_decode_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int64, C.POINTER(C.c_size_t)]
+_lib.bp_decode.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp, _vp, _vp,
+                           _vp]
+_lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64,
+                                 C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.pc_status_string.argtypes = [C.c_int]
+_lib.pc_status_string.restype = C.c_char_p
+
+
+class PcError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {status} ({_lib.pc_status_string(status).decode()})")
+        self.status = status
+
+
+def _check(fn: str, status: int):
+    if status != PC_OK:
+        raise PcError(fn, status)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def library_path() -> str:
+    return str(_LIB_PATH)
+
+
+def sched(mode: int = 0, *, P_range: int = 2, P_level: int = 1, N_min: int = 1, D: int = 0, T0: int = 1,
+          rho_range_fixed: int = 0, q_max: int = 0, it_reset_full: int = 0, stop_from: int = 1,
+          stop_kind: int = 1, fkind: int = 0, alpha: float = 0.9375, seed: int = 0,
+          frame_base: int = 0) -> PcSched:
+    s = PcSched()
+    s.mode, s.P_range, s.P_level, s.N_min, s.D, s.T0 = mode, P_range, P_level, N_min, D, T0
+    s.rho_range_fixed, s.q_max, s.it_reset_full = rho_range_fixed, q_max, it_reset_full
+    s.stop_from, s.stop_kind, s.fkind, s.alpha = stop_from, stop_kind, fkind, alpha
+    s.seed, s.frame_base = seed, frame_base
+    return s
+
+
+def event(level: int, range_: int, block: int, order) -> PcEvent:
+    e = PcEvent()
+    e.level, e.range, e.block = level, range_, block
+    for i in range(16):
+        e.order[i] = order[i] if i < len(order) else i
+    return e
+
+
+def pc_construct(N: int, K: int, crc_len: int = 0, crc_poly: int = 0, design_ebn0_db: float = 0.0) -> PcCode:
+    code = PcCode()
+    _check("pc_construct", _lib.pc_construct(N, K, crc_len, crc_poly, design_ebn0_db, C.byref(code)))
+    return code
+
+
+def pc_encode(code: PcCode, payload, x_out, stream=None):
+    """payload: uint8 CUDA tensor [B, K - crc_len]; x_out: uint8 CUDA tensor [B, N]."""
+    B = x_out.shape[0]
+    _check("pc_encode", _lib.pc_encode(C.byref(code), _ptr(payload), _ptr(x_out), B, _stream(stream)))
+
+
+def bp_decode_workspace_size(code: PcCode, B: int) -> int:
+    out = C.c_size_t(0)
+    _check("bp_decode_workspace_size", _lib.bp_decode_workspace_size(C.byref(code), B, C.byref(out)))
+    return out.value
+
+
+def bp_decode(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, workspace, stream=None):
+    """llr: float32 [B, N]; bits: int32 [B, ceil(K/32)]; iters: int32 [B]; crc_ok: uint8 [B]."""
+    B = llr.shape[0]
+    _check("bp_decode", _lib.bp_decode(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
+                                       _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
+
+
+def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dump, bits, iters, crc_ok, workspace,
+                    stream=None):
+    """As bp_decode, recording every plane into dump [B, max_iters, 2, n+1, N]; events: list of PcEvent or None."""
+    B = llr.shape[0]
+    if events is None:
+        evp, nev = None, 0
+    else:
+        arr = (PcEvent * max(len(events), 1))(*events)
+        evp, nev = arr, len(events)
+    _check("bp_decode_trace", _lib.bp_decode_trace(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, evp, nev,
+                                                   _ptr(dump), _ptr(bits), _ptr(iters), _ptr(crc_ok),
+                                                   _ptr(workspace), _stream(stream)))
+
+
+def words_of(K: int) -> int:
+    return int(math.ceil(K / 32))
+
+
+class Decoder:
+    """Owns the output and workspace tensors of repeated bp_decode calls on one device."""
+
+    def __init__(self, code: PcCode, sch: PcSched, max_iters: int, device="cuda"):
+        import torch
+
+        self.code, self.sched, self.max_iters = code, sch, max_iters
+        self.device = torch.device(device)
+        self._B = -1
+        self.workspace = torch.empty(bp_decode_workspace_size(code, 1), dtype=torch.uint8, device=self.device)
+
+    def _ensure(self, B: int):
+        import torch
+
+        if B != self._B:
+            self.bits = torch.empty((B, words_of(self.code.K)), dtype=torch.int32, device=self.device)
+            self.iters = torch.empty(B, dtype=torch.int32, device=self.device)
+            self.crc_ok = torch.empty(B, dtype=torch.uint8, device=self.device)
+            self._B = B
+
+    def __call__(self, llr, stream=None):
+        self._ensure(llr.shape[0])
+        bp_decode(self.code, llr, self.sched, self.max_iters, self.bits, self.iters, self.crc_ok, self.workspace,
+                  stream)
+        return self.bits, self.iters, self.crc_ok
+
+
+def unpack_bits(words, K: int):
+    """[B, ceil(K/32)] int32 words -> [B, K] uint8 bits (bit k in word k/32 at position k%32)."""
+    import torch
+
+    w = words.to(torch.int64) & 0xFFFFFFFF
+    shifts = torch.arange(32, device=w.device, dtype=torch.int64)
+    bits = (w.unsqueeze(-1) >> shifts) & 1
+    return bits.reshape(w.shape[0], -1)[:, :K].to(torch.uint8)
+
+
+class HostDecoder:
+    """Decodes LLRs that live in (pinned) host memory: the batch is cut into
+    chunks whose host-to-device copies run on a copy stream while earlier
+    chunks decode on the compute stream; results are copied back to host
+    buffers.  Device buffers are allocated once per batch shape."""
+
+    def __init__(self, code: PcCode, sch: PcSched, max_iters: int, device="cuda", chunks: int = 8):
+        import torch
+
+        self.code, self.sched, self.max_iters = code, sch, max_iters
+        self.device = torch.device(device)
+        self.chunks = chunks
+        self.copy_stream = torch.cuda.Stream(self.device)
+        self.compute_stream = torch.cuda.Stream(self.device)
+        self.workspace = [torch.empty(bp_decode_workspace_size(code, 1), dtype=torch.uint8, device=self.device)
+                          for _ in range(chunks)]
+        self._shape = None
+
+    def _ensure(self, B: int):
+        import torch
+
+        if self._shape != B:
+            N, KW = self.code.N, words_of(self.code.K)
+            self.d_llr = torch.empty((B, N), dtype=torch.float32, device=self.device)
+            self.d_bits = torch.empty((B, KW), dtype=torch.int32, device=self.device)
+            self.d_iters = torch.empty(B, dtype=torch.int32, device=self.device)
+            self.d_ok = torch.empty(B, dtype=torch.uint8, device=self.device)
+            self.h_bits = torch.empty((B, KW), dtype=torch.int32, pin_memory=True)
+            self.h_iters = torch.empty(B, dtype=torch.int32, pin_memory=True)
+            self.h_ok = torch.empty(B, dtype=torch.uint8, pin_memory=True)
+            self._shape = B
+
+    def __call__(self, h_llr):
+        """h_llr: pinned float32 [B, N] host tensor -> (bits, iters, crc_ok) host tensors (synchronised)."""
+        import torch
+
+        B = h_llr.shape[0]
+        self._ensure(B)
+        step = (B + self.chunks - 1) // self.chunks
+        done = []
+        for c in range(self.chunks):
+            lo, hi = c * step, min(B, (c + 1) * step)
+            if lo >= hi:
+                break
+            with torch.cuda.stream(self.copy_stream):
+                self.d_llr[lo:hi].copy_(h_llr[lo:hi], non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.copy_stream)
+            self.compute_stream.wait_event(ev)
+            with torch.cuda.stream(self.compute_stream):
+                bp_decode(self.code, self.d_llr[lo:hi], self.sched, self.max_iters, self.d_bits[lo:hi],
+                          self.d_iters[lo:hi], self.d_ok[lo:hi], self.workspace[c], self.compute_stream)
+                self.h_bits[lo:hi].copy_(self.d_bits[lo:hi], non_blocking=True)
+                self.h_iters[lo:hi].copy_(self.d_iters[lo:hi], non_blocking=True)
+                self.h_ok[lo:hi].copy_(self.d_ok[lo:hi], non_blocking=True)
+            done.append((lo, hi))
+        self.compute_stream.synchronize()
+        return self.h_bits, self.h_iters, self.h_ok

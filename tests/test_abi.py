@@ -1,0 +1,146 @@
+"""C ABI checks that need no GPU: the library loads, exports every function
+include/pcbp.h declares, and its host-side logic (construction, argument
+validation) behaves as documented."""
+import ctypes as C
+import re
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+ROOT = Path(__file__).resolve().parent.parent
+
+
+def _has_cuda():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# The validation tests pass placeholder addresses that are only ever checked
+# on the host.  They run only where no GPU exists, so that a validation bug
+# can never turn into a launch on those addresses.
+no_gpu_only = pytest.mark.skipif(_has_cuda(), reason="placeholder pointers: host-only check")
+
+
+def declared_functions():
+    names = []
+    for hdr in sorted((ROOT / "include").glob("*.h")):
+        text = hdr.read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^(?:const\s+)?\w+\s*\*?\s*(\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(pcbp):
+    names = declared_functions()
+    assert "bp_decode" in names and "pc_construct" in names
+    lib = C.CDLL(pcbp.library_path())
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(pcbp.EXPORTED) <= set(names)
+
+
+@pytest.mark.parametrize("N,K,db", [(8, 4, 0.0), (64, 32, 0.0), (256, 128, 0.0), (1024, 512, 0.0),
+                                    (2048, 1024, 0.0), (512, 384, 1.5), (128, 32, -2.0), (2048, 1536, 0.0)])
+def test_pc_construct_matches_oracle(pcbp, oracle, N, K, db):
+    code = pcbp.pc_construct(N, K, 0, 0, db)
+    _, fr = oracle.construct(N, K, db)
+    assert code.N == N and code.n == N.bit_length() - 1 and code.K == K
+    assert np.array_equal(np.array(code.frozen(), dtype=np.uint8), fr)
+    assert code.info_positions() == list(np.nonzero(fr == 0)[0])
+
+
+def test_pc_construct_crc_poly_normalised(pcbp):
+    c8 = pcbp.pc_construct(256, 128, 8, 0x9B)
+    assert c8.crc_poly == 0x19B and c8.crc_len == 8
+    c24 = pcbp.pc_construct(1024, 512, 24, 0x1B2B117)
+    assert c24.crc_poly == 0x1B2B117
+
+
+@pytest.mark.parametrize("args", [(12, 6, 0, 0), (4, 2, 0, 0), (4096, 2048, 0, 0), (64, 0, 0, 0), (64, 65, 0, 0),
+                                  (64, 8, 8, 0x9B), (64, 32, 33, 1), (64, 32, 8, 0x3FF)])
+def test_pc_construct_rejects_bad_arguments(pcbp, args):
+    with pytest.raises(pcbp.PcError) as e:
+        pcbp.pc_construct(*args)
+    assert e.value.status == pcbp.PC_EINVAL
+
+
+def _call_decode(pcbp, code, sch, max_iters=10, B=4, llr=1, bits=1, iters=1, ok=1, ws=256):
+    p = lambda v: C.c_void_p(v) if v else None
+    return pcbp._lib.bp_decode(C.byref(code), p(llr * 4096), C.byref(sch), max_iters, B, p(bits * 4096),
+                               p(iters * 4096), p(ok * 4096), p(ws * 4096), None)
+
+
+@no_gpu_only
+def test_bp_decode_validates_before_touching_the_device(pcbp):
+    """Every argument error returns PC_EINVAL on the host; nothing is launched
+    (these calls run on a machine without a GPU)."""
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    ok = pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=5)
+    bad_scheds = [
+        pcbp.sched(mode=3),
+        pcbp.sched(mode=1, P_range=9, P_level=5, N_min=5, T0=5),          # P_range > n
+        pcbp.sched(mode=1, P_range=3, P_level=8, N_min=5, T0=5),          # P_level > n - 1
+        pcbp.sched(mode=1, P_range=3, P_level=5, N_min=0, T0=5),          # N_min < 1
+        pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=0),          # T0 < 1
+        pcbp.sched(mode=1, rho_range_fixed=1, P_level=5, N_min=5, T0=5),  # rho_range < 2
+        pcbp.sched(mode=2, it_reset_full=0),
+        pcbp.sched(stop_kind=4),
+        pcbp.sched(alpha=0.0),
+        pcbp.sched(alpha=float("nan")),
+    ]
+    for s in bad_scheds:
+        assert _call_decode(pcbp, code, s) == pcbp.PC_EINVAL
+    assert _call_decode(pcbp, code, pcbp.sched(fkind=2)) == pcbp.PC_EUNSUPPORTED
+    assert _call_decode(pcbp, code, ok, max_iters=-1) == pcbp.PC_EINVAL
+    assert _call_decode(pcbp, code, ok, B=-1) == pcbp.PC_EINVAL
+    assert _call_decode(pcbp, code, ok, llr=0) == pcbp.PC_EINVAL
+    assert _call_decode(pcbp, code, ok, bits=0) == pcbp.PC_EINVAL
+    assert _call_decode(pcbp, code, ok, ws=0) == pcbp.PC_EINVAL
+    # misaligned LLR pointer (must be 16-byte aligned)
+    assert pcbp._lib.bp_decode(C.byref(code), C.c_void_p(4096 + 4), C.byref(ok), 10, 4, C.c_void_p(4096),
+                               C.c_void_p(4096), C.c_void_p(4096), C.c_void_p(8192), None) == pcbp.PC_EINVAL
+    # B == 0 is a no-op that succeeds without any device call
+    assert _call_decode(pcbp, code, ok, B=0) == pcbp.PC_OK
+    # a corrupted code (frozen mask inconsistent with K) is rejected
+    bad = pcbp.pc_construct(256, 128, 8, 0x9B)
+    bad.frozen_mask[0] ^= 1
+    assert _call_decode(pcbp, bad, ok) == pcbp.PC_EINVAL
+
+
+@no_gpu_only
+def test_trace_validates_events(pcbp):
+    code = pcbp.pc_construct(64, 32)
+    s = pcbp.sched(mode=1, P_range=3, P_level=4, N_min=2, T0=2)
+    good = pcbp.event(2, 3, 1, [2, 0, 1])
+    bad = [pcbp.event(5, 3, 0, [0, 1, 2]),      # level + range - 1 > n
+           pcbp.event(2, 3, 4, [0, 1, 2]),      # block >= N / 2^m = 4
+           pcbp.event(1, 3, 0, [0, 0, 1]),      # not a permutation
+           pcbp.event(1, 1, 0, [0])]            # range < 2
+    p = C.c_void_p(4096)
+    for ev in bad:
+        arr = (pcbp.PcEvent * 2)(good, ev)
+        assert pcbp._lib.bp_decode_trace(C.byref(code), p, C.byref(s), 5, 2, arr, 2, p, p, p, p, C.c_void_p(8192),
+                                         None) == pcbp.PC_EINVAL
+    arr = (pcbp.PcEvent * 1)(good)
+    assert pcbp._lib.bp_decode_trace(C.byref(code), p, C.byref(s), 5, 2, arr, 1, None, p, p, p, C.c_void_p(8192),
+                                     None) == pcbp.PC_EINVAL   # no dump buffer
+
+
+def test_workspace_size_and_status_strings(pcbp):
+    code = pcbp.pc_construct(1024, 512, 24, 0x1B2B117)
+    assert pcbp.bp_decode_workspace_size(code, 10**6) >= 8
+    assert pcbp._lib.pc_status_string(pcbp.PC_EINVAL) == b"invalid argument"
+    assert pcbp._lib.pc_status_string(12345) == b"unknown status"
+
+
+@no_gpu_only
+def test_pc_encode_validates(pcbp):
+    code = pcbp.pc_construct(64, 32, 8, 0x9B)
+    assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), None, 4, None) == pcbp.PC_EINVAL
+    assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), C.c_void_p(4096), -1, None) == pcbp.PC_EINVAL
+    assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), C.c_void_p(4096), 0, None) == pcbp.PC_OK
