@@ -74,12 +74,18 @@ def measured_peaks():
 
 
 def profiled_traffic(sha: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on this kernel source."""
-    p = ROOT / "profiles" / "bp_decode_n1024_traffic.json"
+    """DRAM bytes per full launch from the committed ncu summary, if it was taken on this kernel source."""
+    p = ROOT / "profiles" / "bp_decode_n1024_pp_s4t10.md"
     if not p.exists():
         return None
-    d = json.loads(p.read_text())
-    return d.get("dram_bytes_per_launch") if d.get("kernel_sha") == sha else None
+    vals = {}
+    for ln in p.read_text().splitlines():
+        if ln.startswith("traffic_"):
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.split()[0]
+    if vals.get("traffic_kernel_sha") != sha:
+        return None
+    return float(vals["traffic_bytes_per_launch_full"])
 
 
 class ClockSampler:

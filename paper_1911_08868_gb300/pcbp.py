@@ -238,7 +238,9 @@ class HostDecoder:
                 ev.record(self.copy_stream)
             self.compute_stream.wait_event(ev)
             with torch.cuda.stream(self.compute_stream):
-                bp_decode(self.code, self.d_llr[lo:hi], self.sched, self.max_iters, self.d_bits[lo:hi],
+                sch = PcSched.from_buffer_copy(self.sched)
+                sch.frame_base = self.sched.frame_base + lo     # chunk frames keep their batch-wide ids
+                bp_decode(self.code, self.d_llr[lo:hi], sch, self.max_iters, self.d_bits[lo:hi],
                           self.d_iters[lo:hi], self.d_ok[lo:hi], self.workspace[c], self.compute_stream)
                 self.h_bits[lo:hi].copy_(self.d_bits[lo:hi], non_blocking=True)
                 self.h_iters[lo:hi].copy_(self.d_iters[lo:hi], non_blocking=True)
