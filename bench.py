@@ -63,8 +63,8 @@ def dist_env():
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_1911_08868_gb300" / "csrc").glob("bp_*")):
-        h.update(p.read_bytes())
+    for name in ("bp_kernel.cuh", "bp_inst.cu"):      # the decoder kernel's source
+        h.update((ROOT / "paper_1911_08868_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:12]
 
 

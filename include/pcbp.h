@@ -152,6 +152,29 @@ int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sch
                     int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
                     void* stream);
 
+/* bp_decode for callers that cannot allocate device memory while they decode,
+ * such as real-time signal-processing pipelines that allocate everything at
+ * start-up (cudaMalloc synchronises the device and has unbounded latency) or
+ * hosts whose device memory belongs to another allocator.  The paper has no
+ * counterpart; this is a deployment variant of bp_decode with the same
+ * arguments except the workspace, and the same results.
+ *   Scratch: the decoder's frame counter lives in a file-scope device array of
+ *     PC_STATIC_SCRATCH_BYTES bytes that every GPU which loads this library
+ *     holds until the process exits.  A call whose decode would need more
+ *     scratch than that returns PC_EUNSUPPORTED.
+ *   Set-up: the first call on a device looks up the array's device address
+ *     (with that device current); make that first call before any stream
+ *     capture.
+ *   Sharing: all calls use the same array, which keeps the last call's
+ *     contents; each call clears the counter on its stream before decoding.
+ *     Calls that overlap on the GPU (other streams, concurrent graph
+ *     replays) race on it and must be serialised by the caller.
+ *   Allocates no device memory (no cudaMalloc or cudaFree). */
+#define PC_STATIC_SCRATCH_BYTES 4096
+int bp_decode_noalloc(const pc_code* code, const float* d_llr, const pc_sched* sched,
+                      int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
+                      uint8_t* d_crc_ok, void* stream);
+
 /* Short text for a status code. */
 const char* pc_status_string(int status);
 

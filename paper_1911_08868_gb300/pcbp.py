@@ -21,7 +21,8 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
-            "pc_status_string")
+            "bp_decode_noalloc", "pc_status_string")
+PC_STATIC_SCRATCH_BYTES = 4096
 
 
 class PcCode(C.Structure):
@@ -55,6 +56,8 @@ _lib.bp_decode.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32
                            _vp]
 _lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64,
                                  C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
+                                   _vp, _vp]
 _lib.pc_status_string.argtypes = [C.c_int]
 _lib.pc_status_string.restype = C.c_char_p
 
@@ -145,6 +148,16 @@ def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dum
     _check("bp_decode_trace", _lib.bp_decode_trace(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, evp, nev,
                                                    _ptr(dump), _ptr(bits), _ptr(iters), _ptr(crc_ok),
                                                    _ptr(workspace), _stream(stream)))
+
+
+def bp_decode_noalloc(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, stream=None):
+    """bp_decode without a workspace argument: for callers that cannot allocate device memory
+    while decoding.  Its scratch is a fixed device array inside the library, shared by every call:
+    calls must not overlap on the GPU, and the first call on a device must precede any stream
+    capture."""
+    B = llr.shape[0]
+    _check("bp_decode_noalloc", _lib.bp_decode_noalloc(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B,
+                                                       _ptr(bits), _ptr(iters), _ptr(crc_ok), _stream(stream)))
 
 
 def words_of(K: int) -> int:
