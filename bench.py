@@ -63,7 +63,7 @@ def dist_env():
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for name in ("bp_kernel.cuh", "bp_inst.cu"):      # the decoder kernel's source
+    for name in ("bp_kernel.cuh", "bp_kernel2.cuh", "bp_inst2.cu"):   # the bp_decode kernel's source
         h.update((ROOT / "paper_1911_08868_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:12]
 

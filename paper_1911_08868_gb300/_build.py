@@ -52,6 +52,10 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         obj = BUILD / f"bp_inst_{n}.o"
         jobs.append((obj, CSRC / "bp_inst.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst.cu"),
                                                 "-o", str(obj)]))
+    for n in LOGNS:
+        obj = BUILD / f"bp_inst2_{n}.o"
+        jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst2.cu"),
+                                                 "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu"):
         obj = BUILD / (Path(name).stem + ".o")
         jobs.append((obj, CSRC / name, [*common, "-c", str(CSRC / name), "-o", str(obj)]))

@@ -80,6 +80,44 @@ cudaError_t launch_of(int n, const BpParams& P, const LaunchGeom& g, bool trace,
     }
 }
 
+#define PCBP_SWITCH_N(n, call)                      \
+    switch (n) {                                    \
+        case 3: call(3); break;                     \
+        case 4: call(4); break;                     \
+        case 5: call(5); break;                     \
+        case 6: call(6); break;                     \
+        case 7: call(7); break;                     \
+        case 8: call(8); break;                     \
+        case 9: call(9); break;                     \
+        case 10: call(10); break;                   \
+        default: call(11); break;                   \
+    }
+
+void shape2_of(int n, int* T, size_t* slot, int* max_slots)
+{
+#define PCBP_SHAPE2(k) bp2_shape_##k(T, slot, max_slots)
+    PCBP_SWITCH_N(n, PCBP_SHAPE2)
+#undef PCBP_SHAPE2
+}
+
+int occupancy2_of(int n, const LaunchGeom& g, int fk)
+{
+    int occ = 0;
+#define PCBP_OCC2(k) occ = bp2_occupancy_##k(g, fk)
+    PCBP_SWITCH_N(n, PCBP_OCC2)
+#undef PCBP_OCC2
+    return occ;
+}
+
+cudaError_t launch2_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+#define PCBP_LAUNCH2(k) e = bp2_launch_##k(P, g, fk, st)
+    PCBP_SWITCH_N(n, PCBP_LAUNCH2)
+#undef PCBP_LAUNCH2
+    return e;
+}
+
 size_t table_bytes(int N, int r, int K)
 {
     const size_t nw = size_t(N >= 32 ? N / 32 : 1);
@@ -106,6 +144,29 @@ int plan_launch(const pc_code* c, int64_t B, bool trace, int fk, LaunchGeom* g)
     g->smem = tab + size_t(slots) * slot;
     g->grid = 1;
     int occ = occupancy_of(c->n, *g, trace, fk);
+    if (occ < 1) return PC_EUNSUPPORTED;
+    const int64_t need = (B + slots - 1) / slots;
+    g->grid = int(std::min<int64_t>(need, int64_t(di.sms) * occ));
+    return PC_OK;
+}
+
+// Stage-grouped kernel: as many slots as shared memory and the block limit allow.
+int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
+{
+    DeviceInfo di;
+    int rc = device_info(&di);
+    if (rc != PC_OK) return rc;
+    int T = 0, max_slots = 0;
+    size_t slot = 0;
+    shape2_of(c->n, &T, &slot, &max_slots);
+    const size_t tab = table_bytes(c->N, c->crc_len, c->K);
+    if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
+    int slots = int((size_t(di.smem_optin) - tab) / slot);
+    slots = std::max(1, std::min(slots, max_slots));
+    g->slots = slots;
+    g->smem = tab + size_t(slots) * slot;
+    g->grid = 1;
+    const int occ = occupancy2_of(c->n, *g, fk);
     if (occ < 1) return PC_EUNSUPPORTED;
     const int64_t need = (B + slots - 1) / slots;
     g->grid = int(std::min<int64_t>(need, int64_t(di.sms) * occ));
@@ -173,12 +234,14 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     P->max_iters = max_iters;
 
     LaunchGeom g;
-    rc = plan_launch(code, B, trace, sched->fkind, &g);
+    rc = trace ? plan_launch(code, B, trace, sched->fkind, &g) : plan_launch2(code, B, sched->fkind, &g);
     if (rc != PC_OK) return rc;
     P->slots = g.slots;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
-    if (launch_of(code->n, *P, g, trace, sched->fkind, st) != cudaSuccess) return PC_ECUDA;
+    const cudaError_t e = trace ? launch_of(code->n, *P, g, true, sched->fkind, st)
+                                : launch2_of(code->n, *P, g, sched->fkind, st);
+    if (e != cudaSuccess) return PC_ECUDA;
     return PC_OK;
 }
 

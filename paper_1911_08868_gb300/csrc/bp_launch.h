@@ -1,5 +1,6 @@
-// Per-length launch entry points of the decoder kernels (one set per n,
-// defined in bp_inst.cu compiled with PCBP_LOGN = n).
+// Per-length launch entry points of the decoder kernels (one set per n):
+// bp_* from bp_inst.cu (per-stage kernel, used for the trace entry), bp2_*
+// from bp_inst2.cu (stage-grouped kernel, used by bp_decode).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -17,7 +18,10 @@ struct LaunchGeom {
 #define PCBP_DECLARE_LEN(n)                                                                              \
     void bp_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out);                                \
     int bp_occupancy_##n(const LaunchGeom& g, bool trace, int fkind);                                    \
-    cudaError_t bp_launch_##n(const BpParams& P, const LaunchGeom& g, bool trace, int fkind, cudaStream_t st);
+    cudaError_t bp_launch_##n(const BpParams& P, const LaunchGeom& g, bool trace, int fkind, cudaStream_t st); \
+    void bp2_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out);            \
+    int bp2_occupancy_##n(const LaunchGeom& g, int fkind);                                                \
+    cudaError_t bp2_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st);
 
 PCBP_DECLARE_LEN(3)
 PCBP_DECLARE_LEN(4)

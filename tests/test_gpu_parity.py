@@ -163,6 +163,20 @@ def test_decode_outputs_bit_exact(pcbp, oracle, case):
     assert (iters < max_iters).any()
 
 
+@pytest.mark.parametrize("N,K", [(16, 8), (64, 32), (256, 128), (1024, 512)])
+def test_decode_small_subgraph_events_bit_exact(pcbp, oracle, N, K):
+    """rho_range = 2 starting at level 1 (m = 2): the permuted stages are
+    narrower than a register group and take the per-PE path of the decoder."""
+    fr, pay, x, llr = frames(oracle, N, K, 0, 0, 300, 1.5, seed=N + 11)
+    s = pcbp.sched(mode=1, P_range=2, P_level=1, N_min=2, T0=2, seed=21, stop_kind=2)
+    code = pcbp.pc_construct(N, K)
+    bits, iters, ok, _ = gpu_decode(pcbp, code, llr, s, 40)
+    rbits, riters, rok = oracle_outputs(oracle, fr, 0, 0, llr, osched(oracle, s), 40)
+    assert np.array_equal(iters, riters)
+    assert np.array_equal(bits, rbits)
+    assert (iters > 2).any()
+
+
 def test_edge_sizes_and_degenerate_cases(pcbp, oracle):
     cases = [
         (8, 8, 0, 0, dict(mode=0, stop_kind=0), 3, 5),        # K = N: nothing frozen, no stop
