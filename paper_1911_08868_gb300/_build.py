@@ -52,10 +52,12 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         obj = BUILD / f"bp_inst_{n}.o"
         jobs.append((obj, CSRC / "bp_inst.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst.cu"),
                                                 "-o", str(obj)]))
+    kb = os.environ.get("PCBP_KB")      # register-group width override (2^KB positions per thread)
     for n in LOGNS:
-        obj = BUILD / f"bp_inst2_{n}.o"
-        jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst2.cu"),
-                                                 "-o", str(obj)]))
+        obj = BUILD / (f"bp_inst2_{n}_kb{int(kb)}.o" if kb else f"bp_inst2_{n}.o")
+        extra = [f"-DPCBP_KB={int(kb)}"] if kb else []
+        jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
+                                                 str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu"):
         obj = BUILD / (Path(name).stem + ".o")
         jobs.append((obj, CSRC / name, [*common, "-c", str(CSRC / name), "-o", str(obj)]))
@@ -87,11 +89,15 @@ def build(verbose: bool = False, force: bool = False) -> Path:
                 if verbose and msg:
                     print(msg)
     objs = [str(j[0]) for j in jobs]
-    if force or todo or not LIB.exists() or any(Path(o).stat().st_mtime > LIB.stat().st_mtime for o in objs):
+    stamp = BUILD / "link_inputs.txt"          # relink when the set of objects changes
+    same_set = stamp.exists() and stamp.read_text() == "\n".join(objs)
+    if (force or todo or not same_set or not LIB.exists()
+            or any(Path(o).stat().st_mtime > LIB.stat().st_mtime for o in objs)):
         cmd = [_nvcc(), *ARCH, "-shared", "-o", str(LIB), *objs]
         res = subprocess.run(cmd, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")
+        stamp.write_text("\n".join(objs))
     return LIB
 
 

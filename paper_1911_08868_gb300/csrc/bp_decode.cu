@@ -159,7 +159,7 @@ int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
     int T = 0, max_slots = 0;
     size_t slot = 0;
     shape2_of(c->n, &T, &slot, &max_slots);
-    const size_t tab = table_bytes(c->N, c->crc_len, c->K);
+    const size_t tab = table_bytes(c->N, c->crc_len, c->K) + 64;   // + the 64-byte swizzle table
     if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(di.smem_optin) - tab) / slot);
     slots = std::max(1, std::min(slots, max_slots));

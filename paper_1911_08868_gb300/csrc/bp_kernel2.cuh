@@ -35,16 +35,26 @@
 
 namespace pcbp {
 
-// Position j is stored at swz(j) in every plane: the bits 5.. are folded onto
-// the bank bits.  swz is linear over XOR and its own inverse.
-template <int LOGN>
-__host__ __device__ __forceinline__ int swz(int j)
+// Position j is stored at j ^ h(j >> 5) in every plane, h linear over GF(2):
+// bit b >= 5 of j flips the bank bits kSwzCol[b - 5].  The columns are
+// chosen (by exhaustive search) so that for every group whose register bits
+// are a contiguous run, the five bits that vary across a warp's lanes map to
+// five independent bank bits: such accesses are free of bank conflicts.  The
+// map is its own inverse.  Kernels keep h(i), i < 64, as a byte table in
+// shared memory.
+constexpr int kSwzTableBytes = 64;
+
+__device__ __forceinline__ unsigned char swz_row(int i)
 {
-    if (LOGN <= 5) return j;
-    int s = j >> 5;
-    if (LOGN > 10) s ^= j >> 10;
-    return j ^ (s & 31);
+    constexpr unsigned cols = 0x04u | (0x09u << 5) | (0x12u << 10) | (0x1Cu << 15) | (0x07u << 20) | (0x0Eu << 25);
+    unsigned h = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+        if ((i >> b) & 1) h ^= (cols >> (5 * b)) & 31u;
+    return (unsigned char)h;
 }
+
+__device__ __forceinline__ int swz(const unsigned char* tab, int j) { return j ^ tab[j >> 5]; }
 
 template <int LOGN, int KB>
 struct G2 {
@@ -82,8 +92,8 @@ struct GroupCtl {
 
 // Partition of the stages of one iteration (slot leader).
 template <int LOGN, int KB>
-__device__ inline void build_groups(GroupCtl<LOGN, KB>* c, bool have_ev, int level, int range, long long blk,
-                                    const signed char* order)
+__device__ inline void build_groups(GroupCtl<LOGN, KB>* c, const unsigned char* swt, bool have_ev, int level,
+                                    int range, long long blk, const signed char* order)
 {
     using C = G2<LOGN, KB>;
     constexpr int n = LOGN;
@@ -155,7 +165,7 @@ __device__ inline void build_groups(GroupCtl<LOGN, KB>* c, bool have_ev, int lev
                     int off = 0;
                     for (int i = 0; i < KB; ++i)
                         if ((e >> i) & 1) off |= 1 << c->P[ng][cls][i];
-                    c->swoff[ng][cls][e] = (short)swz<LOGN>(off);
+                    c->swoff[ng][cls][e] = (short)swz(swt, off);
                 }
             }
             ++ng;
@@ -190,7 +200,7 @@ __device__ __forceinline__ int group_base(const GroupCtl<LOGN, KB>* c, int gi, i
 // ---------------------------------------------------------------------------
 // Largest block of the grouped kernel: slots x threads per slot never exceed it.
 template <int KB>
-__host__ __device__ constexpr int grouped_max_threads() { return KB >= 4 ? 384 : 512; }
+__host__ __device__ constexpr int grouped_max_threads() { return KB >= 4 ? 384 : (KB == 3 ? 512 : 768); }
 
 template <int LOGN, int KB, int FK>
 __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_grouped_kernel(const __grid_constant__ BpParams P)
@@ -209,7 +219,10 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
     for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
     for (int i = threadIdx.x; i < r * NW; i += blockDim.x) s_crc[i] = P.code.crcplane[i / NW][i % NW];
     for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    unsigned char* s_swz = smem + shared_table_bytes(NW, r, K);
+    for (int i = threadIdx.x; i < kSwzTableBytes; i += blockDim.x) s_swz[i] = swz_row(i);
     __syncthreads();
+    auto sw = [&](int j) { return swz(s_swz, j); };
 
     const int slot = threadIdx.x / T;
     const int tid = threadIdx.x - slot * T;
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
     const bool owner = tid < TA;
     constexpr size_t ctl_bytes = align16(sizeof(Ctl));
     constexpr size_t slot_sz = ctl_bytes + align16(2 * NW * 4) + size_t(2 * C::NPL) * N * 4;
-    unsigned char* sbase = smem + shared_table_bytes(NW, r, K) + size_t(slot) * slot_sz;
+    unsigned char* sbase = smem + shared_table_bytes(NW, r, K) + kSwzTableBytes + size_t(slot) * slot_sz;
     Ctl* ctl = reinterpret_cast<Ctl*>(sbase);
     uint32_t* dec = reinterpret_cast<uint32_t*>(sbase + ctl_bytes);
     uint32_t* xh = dec + NW;
@@ -245,7 +258,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
         if (f >= P.B) break;
         const float* llr_f = P.llr + size_t(f) * N;
 
-        for (int i = tid; i < C::NPL * N; i += T) Rp[i] = 0.f;
+        for (int i = tid; i < C::NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = tid; i < NW; i += T) dec[i] = 0u;
         if (tid == 0) {
             ctl->have_ev = 0;
@@ -254,7 +267,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
             ctl->ev_range = 0;
             ctl->ev_blk = -1;
             signed char none[16];
-            build_groups<LOGN, KB>(ctl, false, 0, 0, 0, none);
+            build_groups<LOGN, KB>(ctl, s_swz, false, 0, 0, 0, none);
         }
         sync();
 
@@ -262,9 +275,9 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
         auto load_l1 = [&]() {
             if (!ctl->single_[0] && owner) {
                 const int cls = (ctl->local[0] && ((tid & ((1 << ctl->low) - 1)) == ctl->beta)) ? 1 : 0;
-                const int bs = swz<LOGN>(group_base<LOGN, KB>(ctl, 0, cls, tid));
+                const int bs = sw(group_base<LOGN, KB>(ctl, 0, cls, tid));
 #pragma unroll
-                for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + swz<LOGN>(bs ^ ctl->swoff[0][cls][e]));
+                for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + sw(bs ^ ctl->swoff[0][cls][e]));
             }
         };
         load_l1();
@@ -296,12 +309,12 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                             if (s >= lo && s <= m1 && (q & lowmask) == ctl->beta) p = ctl->pbit[s];
                             const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
                             const int b = t | (1 << p);
-                            const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + swz<LOGN>(t)];
-                            const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + swz<LOGN>(b)];
-                            const float rt = Rp[s * N + swz<LOGN>(t)];
-                            const float rb = Rp[s * N + swz<LOGN>(b)];
-                            Lp[s * N + swz<LOGN>(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
-                            Lp[s * N + swz<LOGN>(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
+                            const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
+                            const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
+                            const float rt = Rp[s * N + sw(t)];
+                            const float rb = Rp[s * N + sw(b)];
+                            Lp[s * N + sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
+                            Lp[s * N + sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
                         }
                     }
                     sync();
@@ -309,7 +322,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 }
                 if (owner) {
                     const int cls = (ctl->local[gi] && inb) ? 1 : 0;
-                    const int bs = swz<LOGN>(group_base<LOGN, KB>(ctl, gi, cls, tid));
+                    const int bs = sw(group_base<LOGN, KB>(ctl, gi, cls, tid));
                     int ph[E];
                     float x[E];
 #pragma unroll
@@ -348,7 +361,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
             float x[E];
             int phL[E];
             if (owner) {
-                const int bs = swz<LOGN>(group_base<LOGN, KB>(ctl, gL, clsL, tid));
+                const int bs = sw(group_base<LOGN, KB>(ctl, gL, clsL, tid));
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     phL[e] = bs ^ ctl->swoff[gL][clsL][e];
@@ -362,7 +375,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
                             xL[i][e] = x[e];
-                            rv[e] = s < n - 1 ? Rp[s * N + phL[e]] : prior_of(s_frozen, swz<LOGN>(phL[e]));
+                            rv[e] = s < n - 1 ? Rp[s * N + phL[e]] : prior_of(s_frozen, sw(phL[e]));
                         }
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
@@ -385,7 +398,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                         int rev = 0;
 #pragma unroll
                         for (int i = 0; i < KB; ++i) rev |= ((e >> i) & 1) << (KB - 1 - i);
-                        const int j = swz<LOGN>(phL[e]);
+                        const int j = sw(phL[e]);
                         if (__fadd_rn(x[e], prior_of(s_frozen, j)) < 0.f) chunk |= 1u << rev;
                     }
                 }
@@ -404,7 +417,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 if (owner) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) {
-                        const int j = swz<LOGN>(phL[e]);
+                        const int j = sw(phL[e]);
                         if (__fadd_rn(x[e], prior_of(s_frozen, j)) < 0.f) atomicOr(&dec[j >> 5], 1u << (j & 31));
                     }
                 }
@@ -436,7 +449,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
             if (owner) {
                 float y[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) y[e] = prior_of(s_frozen, swz<LOGN>(phL[e]));   // R(n+1): the last group ends at stage n
+                for (int e = 0; e < E; ++e) y[e] = prior_of(s_frozen, sw(phL[e]));   // R(n+1): the last group ends at stage n
 #pragma unroll
                 for (int i = KB - 1; i >= 0; --i) {
                     if (i < glL) {
@@ -456,7 +469,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                         } else {
 #pragma unroll
                             for (int e = 0; e < E; ++e) {
-                                const int j = swz<LOGN>(phL[e]);
+                                const int j = sw(phL[e]);
                                 if (__fadd_rn(L1[e], y[e]) < 0.f) atomicOr(&xh[j >> 5], 1u << (j & 31));
                             }
                         }
@@ -480,15 +493,15 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                                 if (s >= lo && s <= m1 && (q & lowmask) == ctl->beta) p = ctl->pbit[s];
                                 const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
                                 const int b = t | (1 << p);
-                                const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + swz<LOGN>(t)];
-                                const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + swz<LOGN>(b)];
-                                const float rt = Rp[s * N + swz<LOGN>(t)];
-                                const float rb = Rp[s * N + swz<LOGN>(b)];
+                                const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
+                                const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
+                                const float rt = Rp[s * N + sw(t)];
+                                const float rb = Rp[s * N + sw(b)];
                                 const float o1 = fnode<FK>(rt, __fadd_rn(lb, rb), alpha);
                                 const float o2 = __fadd_rn(fnode<FK>(rt, lt, alpha), rb);
                                 if (s >= 1) {
-                                    Rp[(s - 1) * N + swz<LOGN>(t)] = o1;
-                                    Rp[(s - 1) * N + swz<LOGN>(b)] = o2;
+                                    Rp[(s - 1) * N + sw(t)] = o1;
+                                    Rp[(s - 1) * N + sw(b)] = o2;
                                 } else {
                                     if (__fadd_rn(lt, o1) < 0.f) atomicOr(&xh[t >> 5], 1u << (t & 31));
                                     if (__fadd_rn(lb, o2) < 0.f) atomicOr(&xh[b >> 5], 1u << (b & 31));
@@ -501,7 +514,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 }
                 if (owner) {
                     const int cls = (ctl->local[gi] && inb) ? 1 : 0;
-                    const int bs = swz<LOGN>(group_base<LOGN, KB>(ctl, gi, cls, tid));
+                    const int bs = sw(group_base<LOGN, KB>(ctl, gi, cls, tid));
                     int ph[E];
                     float y[E];
 #pragma unroll
@@ -531,7 +544,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                             } else {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) {
-                                    const int j = swz<LOGN>(ph[e]);
+                                    const int j = sw(ph[e]);
                                     if (__fadd_rn(L1[e], y[e]) < 0.f) atomicOr(&xh[j >> 5], 1u << (j & 31));
                                 }
                             }
@@ -588,7 +601,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                             inc = qz > S.N_min ? qz : S.N_min;
                         }
                         ctl->next_inc = int(inc);
-                        build_groups<LOGN, KB>(ctl, true, level, range, blk, order);
+                        build_groups<LOGN, KB>(ctl, s_swz, true, level, range, blk, order);
                     }
                     sync();
                     // resetVariableNodes: R at the interior levels of the previous
@@ -603,7 +616,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                         for (int i = tid; i < (rg - 1) * span; i += T) {
                             const int lev = lv + 1 + i / span;       // node level, 2..n
                             const int j = int(bk) + ((i & (span - 1)) << (n - m));
-                            Rp[(lev - 2) * N + swz<LOGN>(j)] = 0.f;
+                            Rp[(lev - 2) * N + sw(j)] = 0.f;
                         }
                     }
                     next_reset = it + ctl->next_inc;
