@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="wall-time budget of the CPU oracle sample")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     return ap.parse_args()
 
 
@@ -206,6 +207,95 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+MIXED_FRAMES = 1 << 20
+MIXED_LENGTHS = (128, 256, 512, 1024, 2048)
+MIXED_RATES = (0.25, 0.5, 0.75)
+
+
+def mixed_sched(pcbp, n, seed):
+    return pcbp.sched(mode=1, rho_range_fixed=4, P_level=n - 1, N_min=10, D=0, T0=10, stop_from=1,
+                      stop_kind=1, alpha=0.9375, seed=seed)
+
+
+def run_mixed(pcbp, inputs, dev, steps, warmup):
+    """2^20 frames, N uniform on {128..2048}, rate uniform on {1/4, 1/2, 3/4}, Eb/N0 uniform on
+    [1, 4] dB per frame, PP-BP s=4 T=10: 15 per-size bp_decode launches against one
+    persistent mixed launch (slots from the autotuner), both also replayed from CUDA graphs."""
+    import numpy as np
+    import torch
+
+    from paper_1911_08868_gb300 import autotune
+
+    rng = np.random.default_rng(7)
+    classes = [(N, R) for N in MIXED_LENGTHS for R in MIXED_RATES]
+    counts = rng.multinomial(MIXED_FRAMES, [1 / len(classes)] * len(classes))
+    slots = autotune.tune_slots(MIXED_LENGTHS, lambda n: mixed_sched(pcbp, n, 1), max_iters=MAX_ITERS, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(4321)
+    parts, info_bits = [], 0
+    order = sorted(range(len(classes)), key=lambda i: -classes[i][0] * counts[i])
+    for ci in order:
+        (N, R), B = classes[ci], int(counts[ci])
+        K = int(N * R)
+        r, poly = autotune.crc_for(N)
+        code = pcbp.pc_construct(N, K, r, poly)
+        pay = inputs.payload_torch(gen, B, K - r, dev)
+        x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+        pcbp.pc_encode(code, pay, x)
+        ebn0 = 1.0 + 3.0 * torch.rand(B, generator=gen, device=dev, dtype=torch.float64)
+        llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0.cpu().numpy(), K, r, N)).contiguous()
+        del x
+        sch = mixed_sched(pcbp, N.bit_length() - 1, 1000 + ci)
+        parts.append((code, sch, MAX_ITERS, llr, slots[N]))
+        info_bits += B * (K - r)
+    decs = [pcbp.Decoder(p[0], p[1], p[2], dev) for p in parts]
+    md = pcbp.MixedDecoder(parts, dev)
+    stream = torch.cuda.Stream(dev)
+
+    def per_size():
+        for d, p in zip(decs, parts):
+            d(p[3], stream)
+
+    def mixed():
+        md(stream)
+
+    def timed(fn, reps):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+            stream.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for _ in range(reps):
+                fn()
+            t1.record(stream)
+            stream.synchronize()
+        return t0.elapsed_time(t1) / reps
+
+    reps = max(1, min(steps, 5))
+    t_per = timed(per_size, reps)
+    t_mix = timed(mixed, reps)
+    same = all(torch.equal(md.iters[i], decs[i].iters) and torch.equal(md.bits[i], decs[i].bits)
+               for i in range(len(parts)))
+    graphs = {}
+    for name, fn in (("per_size", per_size), ("mixed", mixed)):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            with torch.cuda.graph(g, stream=stream):
+                fn()
+        graphs[name] = timed(g.replay, reps)
+    return {"frames": int(MIXED_FRAMES), "classes": len(classes), "launches_per_size": len(parts),
+            "per_size_ms": t_per, "mixed_ms": t_mix, "per_size_graph_ms": graphs["per_size"],
+            "mixed_graph_ms": graphs["mixed"], "speedup": t_per / t_mix,
+            "speedup_graphs": graphs["per_size"] / graphs["mixed"],
+            "mixed_gbit_s": info_bits / (graphs["mixed"] / 1e3) / 1e9,
+            "slots": {str(k): v for k, v in slots.items()}, "outputs_identical": bool(same),
+            "workload": "2^20 frames, N~U{128..2048}, R~U{1/4,1/2,3/4}, Eb/N0~U[1,4] dB, PP-BP s=4 T=10, "
+                        "max 300 it, CRC-8 (N<=256) / CRC-24"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -336,6 +426,11 @@ def run_ours(args):
                            "h2d_bytes_per_step": B * N * 4,
                            "d2h_bytes_per_step": B * (4 * math.ceil(K / 32) + 4 + 1), "steps": e_steps,
                            "chunks": hdec.chunks, "matches_device_run": same}
+
+    if rank == 0 and not args.no_mixed:
+        del dec
+        torch.cuda.empty_cache()
+        line["mixed"] = run_mixed(pcbp, inputs, dev, args.steps, args.warmup)
 
     if rank == 0 and not args.no_cpu:
         cb = cpu_oracle(args.cpu_seconds)

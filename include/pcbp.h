@@ -152,6 +152,43 @@ int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sch
                     int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
                     void* stream);
 
+/* ---- Mixed-length batched decoding (one persistent launch) ----------------
+ * Several batches, each with its own code (any supported N and rate), schedule
+ * and buffers, decoded by one launch whose CTAs drain the batches in order
+ * (each CTA re-shapes its frame slots for each batch's N).  Results are those
+ * of bp_decode on each batch alone (same frame ids, same arithmetic).
+ * Batches are processed in the order given: put the longest work first.
+ * Scaled min-sum only (fkind 0). */
+#define PC_MAX_BATCHES 64
+
+typedef struct {
+    const pc_code* code;      /* host pointer */
+    pc_sched sched;           /* frame b draws events with frame id sched.frame_base + b */
+    int32_t max_iters;
+    int32_t slots;            /* frames resident per CTA; 0 = as many as fit */
+    int64_t B;                /* frames in this batch */
+    const float* d_llr;       /* B x N, 16-byte aligned */
+    uint32_t* d_bits;         /* B x ceil(K/32) */
+    int32_t* d_iters;         /* B */
+    uint8_t* d_crc_ok;        /* B */
+} pc_batch;
+
+/* Bytes of the device descriptor table of n_batches batches. */
+int bp_mixed_table_size(int32_t n_batches, size_t* bytes);
+/* Writes the descriptor table of the batches (code tables, schedules,
+ * buffer pointers, slot counts for the current device) into host memory
+ * h_table; the caller copies it to device memory once and passes that copy
+ * to bp_decode_mixed.  Host only (reads the current device's limits). */
+int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes);
+/* Bytes of device workspace of bp_decode_mixed (one frame counter per batch). */
+int bp_mixed_workspace_size(int32_t n_batches, size_t* bytes);
+/* Decodes all batches with one kernel launch (after clearing the counters
+ * in d_workspace).  d_table: the uploaded output of bp_mixed_prepare for the
+ * same batches, 16-byte aligned.  Enqueues only a memset and a launch, so it
+ * can be captured in a CUDA graph (make one uncaptured call first). */
+int bp_decode_mixed(const pc_batch* batches, int32_t n_batches, void* d_table, void* d_workspace,
+                    void* stream);
+
 /* bp_decode for callers that cannot allocate device memory while they decode,
  * such as real-time signal-processing pipelines that allocate everything at
  * start-up (cudaMalloc synchronises the device and has unbounded latency) or

@@ -1,0 +1,86 @@
+"""Autotuner of the frames resident per CTA ("slots") of the mixed-length launch.
+
+For each code length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the
+given Eb/N0, the given schedule) with every candidate slot count through a
+single-batch MixedDecoder, times the launches with CUDA events and keeps the
+fastest.  Results are cached per GPU name in a JSON file
+($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
+"""
+from __future__ import annotations
+
+import json
+import os
+from pathlib import Path
+
+CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
+
+
+def cache_path() -> Path:
+    return Path(os.environ.get("PCBP_TUNE_CACHE", str(Path.home() / ".cache" / "pcbp_tune.json")))
+
+
+def crc_for(N: int):
+    return (8, 0x9B) if N <= 256 else (24, 0x1B2B117)
+
+
+def _synthetic(pcbp, inputs, dev, N, K, r, poly, B, ebn0, seed):
+    import torch
+
+    code = pcbp.pc_construct(N, K, r, poly)
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    pay = inputs.payload_torch(gen, B, K - r, dev)
+    x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+    pcbp.pc_encode(code, pay, x)
+    llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0, K, r, N)).contiguous()
+    return code, llr
+
+
+def tune_slots(lengths, sched_for, max_iters: int = 300, frames: int = 16384, ebn0: float = 2.5,
+               device="cuda", use_cache: bool = True, reps: int = 3) -> dict:
+    """Best slot count per length.  sched_for(n) returns the pc_sched for log2 N = n."""
+    import torch
+
+    from . import inputs, pcbp
+
+    dev = torch.device(device)
+    key = f"{torch.cuda.get_device_name(dev)}|{pcbp.library_path()}|{max_iters}|{frames}|{ebn0}"
+    cache = {}
+    cp = cache_path()
+    if use_cache and cp.exists():
+        try:
+            cache = json.loads(cp.read_text())
+        except (OSError, ValueError):
+            cache = {}
+    entry = cache.get(key, {})
+    best = {}
+    for N in lengths:
+        if str(N) in entry:
+            best[N] = int(entry[str(N)])
+            continue
+        K = N // 2
+        r, poly = crc_for(N)
+        code, llr = _synthetic(pcbp, inputs, dev, N, K, r, poly, frames, ebn0, seed=N)
+        sch = sched_for(N.bit_length() - 1)
+        times = {}
+        for slots in CANDIDATES:
+            md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots)], dev)
+            md()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            for _ in range(reps):
+                md()
+            t1.record()
+            torch.cuda.synchronize()
+            times[slots] = t0.elapsed_time(t1) / reps
+        best[N] = min(times, key=lambda s: (times[s], -s))
+        entry[str(N)] = best[N]
+    if use_cache:
+        cache[key] = entry
+        try:
+            cp.parent.mkdir(parents=True, exist_ok=True)
+            cp.write_text(json.dumps(cache, indent=1))
+        except OSError:
+            pass
+    return best

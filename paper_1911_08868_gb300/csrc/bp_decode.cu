@@ -232,6 +232,15 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     P->dump = d_dump;
     P->B = B;
     P->max_iters = max_iters;
+    P->job.S = P->sched;
+    P->job.llr = d_llr;
+    P->job.bits = d_bits;
+    P->job.iters = d_iters;
+    P->job.crc_ok = d_crc_ok;
+    P->job.B = B;
+    P->job.max_iters = max_iters;
+    P->job.K = code->K;
+    P->job.r = code->crc_len;
 
     LaunchGeom g;
     rc = trace ? plan_launch(code, B, trace, sched->fkind, &g) : plan_launch2(code, B, sched->fkind, &g);

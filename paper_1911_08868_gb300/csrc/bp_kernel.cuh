@@ -94,7 +94,7 @@ __device__ __forceinline__ uint64_t event_draw(uint64_t seed, uint64_t frame, ui
 // draws a full order (level 1, range n, one block).  The stage order is a
 // uniform non-identity permutation: Fisher-Yates, redrawn while identity, a
 // rotation after 8 identity draws.
-__device__ inline void draw_event(const DevSched& S, int n, uint64_t frame, int k, int& level, int& range,
+static __device__ __noinline__ void draw_event(const DevSched& S, int n, uint64_t frame, int k, int& level, int& range,
                                   long long& block, signed char* order)
 {
     if (S.mode == 2) {

@@ -91,12 +91,10 @@ struct GroupCtl {
 };
 
 // Partition of the stages of one iteration (slot leader).
-template <int LOGN, int KB>
-__device__ inline void build_groups(GroupCtl<LOGN, KB>* c, const unsigned char* swt, bool have_ev, int level,
-                                    int range, long long blk, const signed char* order)
+template <int CL, int KB>
+__device__ __noinline__ void build_groups(GroupCtl<CL, KB>* c, const unsigned char* swt, int n, bool have_ev,
+                                          int level, int range, long long blk, const signed char* order)
 {
-    using C = G2<LOGN, KB>;
-    constexpr int n = LOGN;
     int lo = n, hi = -1, m = 0;
     if (have_ev) {
         lo = level - 1;
@@ -181,8 +179,8 @@ __device__ inline void build_groups(GroupCtl<LOGN, KB>* c, const unsigned char* 
     c->fastdec = fast ? 1 : 0;
 }
 
-template <int LOGN, int KB>
-__device__ __forceinline__ int group_base(const GroupCtl<LOGN, KB>* c, int gi, int cls, int tid)
+template <int CL, int KB>
+__device__ __forceinline__ int group_base(const GroupCtl<CL, KB>* c, int gi, int cls, int tid)
 {
     const int a = c->contig[gi][cls];
     if (a >= 0) return (tid & ((1 << a) - 1)) | ((tid >> a) << (a + KB));
@@ -202,26 +200,85 @@ __device__ __forceinline__ int group_base(const GroupCtl<LOGN, KB>* c, int gi, i
 template <int KB>
 __host__ __device__ constexpr int grouped_max_threads() { return KB >= 4 ? 384 : (KB == 3 ? 512 : 768); }
 
-template <int LOGN, int KB, int FK>
-__global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_grouped_kernel(const __grid_constant__ BpParams P)
+// Code tables in shared memory: frozen mask, CRC bit-planes, information
+// positions, swizzle table; the frame slots follow.  Returns the slot area.
+__device__ __forceinline__ unsigned char* load_code_tables(const DevCode& code, unsigned char* smem)
 {
-    using C = G2<LOGN, KB>;
-    using Ctl = GroupCtl<LOGN, KB>;
-    constexpr int N = C::N, n = C::n, E = C::E, TA = C::TA, T = C::T, NW = C::NW;
-    constexpr int NWARP = T / 32;
-    extern __shared__ __align__(16) unsigned char smem[];
-
-    const int r = P.code.r;
-    const int K = P.code.K;
+    const int NW = code.N >= 32 ? code.N / 32 : 1;
+    const int r = code.r, K = code.K;
     uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
     uint32_t* s_crc = s_frozen + NW;
     int16_t* s_info = reinterpret_cast<int16_t*>(s_crc + r * NW);
-    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
-    for (int i = threadIdx.x; i < r * NW; i += blockDim.x) s_crc[i] = P.code.crcplane[i / NW][i % NW];
-    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = code.frozen[i];
+    for (int i = threadIdx.x; i < r * NW; i += blockDim.x) s_crc[i] = code.crcplane[i / NW][i % NW];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = code.info_idx[i];
     unsigned char* s_swz = smem + shared_table_bytes(NW, r, K);
     for (int i = threadIdx.x; i < kSwzTableBytes; i += blockDim.x) s_swz[i] = swz_row(i);
-    __syncthreads();
+    return s_swz + kSwzTableBytes;
+}
+
+// G-matrix test for a length known only at run time (one warp); see g_check.
+__device__ __forceinline__ bool g_check_rt(const uint32_t* dec, const uint32_t* xh, int lane, int n)
+{
+    const int NW = n >= 5 ? 1 << (n - 5) : 1;
+    uint32_t v[2];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int w = lane + 32 * e;
+        v[e] = w < NW ? dec[w] : 0u;
+    }
+    const uint32_t masks[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
+    for (int p = 0; p < (n < 5 ? n : 5); ++p)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) v[e] ^= (v[e] >> (1 << p)) & masks[p];
+    for (int p = 5; p < n; ++p) {
+        const int q = p - 5;
+        if (q < 5) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const uint32_t other = __shfl_xor_sync(0xffffffffu, v[e], 1 << q);
+                if (!((lane >> q) & 1)) v[e] ^= other;
+            }
+        } else {
+            v[0] ^= v[1];
+        }
+    }
+    bool ok = true;
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int w = lane + 32 * e;
+        if (w < NW) ok = ok && (v[e] == xh[w]);
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Decodes frames of one job until the counter passes B (J may live in
+// parameter or global memory: it is read where it is).  Threads
+// [0, nslots * T) take part, in slots of T threads; the code tables are
+// already in shared memory (load_code_tables) and visible to all of them.
+// LOGN = 0: the length comes from n_rt at run time (one body for every
+// length); otherwise every geometric quantity below is a constant.
+template <int LOGN, int KB, int FK>
+__device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long long* counter,
+                                               unsigned char* smem, int n_rt)
+{
+    constexpr int CL = LOGN ? LOGN : kMaxLogN;
+    using Ctl = GroupCtl<CL, KB>;
+    const int n = LOGN ? LOGN : n_rt;
+    const int N = 1 << n;
+    constexpr int E = 1 << KB;
+    const int TA = N / E;
+    const int T = TA < 32 ? 32 : TA;
+    const int NW = N >= 32 ? N / 32 : 1;
+    const int NWARP = T / 32;
+    const int NPL = n - 1;
+
+    const int r = J.r;
+    const int K = J.K;
+    const uint32_t* s_frozen = reinterpret_cast<const uint32_t*>(smem);
+    const uint32_t* s_crc = s_frozen + NW;
+    const int16_t* s_info = reinterpret_cast<const int16_t*>(s_crc + r * NW);
+    const unsigned char* s_swz = smem + shared_table_bytes(NW, r, K);
     auto sw = [&](int j) { return swz(s_swz, j); };
 
     const int slot = threadIdx.x / T;
@@ -230,35 +287,35 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
     const int warp = tid >> 5;
     const bool owner = tid < TA;
     constexpr size_t ctl_bytes = align16(sizeof(Ctl));
-    constexpr size_t slot_sz = ctl_bytes + align16(2 * NW * 4) + size_t(2 * C::NPL) * N * 4;
+    const size_t slot_sz = ctl_bytes + align16(size_t(2 * NW * 4)) + size_t(2 * NPL) * N * 4;
     unsigned char* sbase = smem + shared_table_bytes(NW, r, K) + kSwzTableBytes + size_t(slot) * slot_sz;
     Ctl* ctl = reinterpret_cast<Ctl*>(sbase);
     uint32_t* dec = reinterpret_cast<uint32_t*>(sbase + ctl_bytes);
     uint32_t* xh = dec + NW;
     float* Lp = reinterpret_cast<float*>(sbase + ctl_bytes + align16(2 * NW * 4));  // level l at (l-2)*N
-    float* Rp = Lp + C::NPL * N;                                                      // level l at (l-2)*N
+    float* Rp = Lp + NPL * N;                                                         // level l at (l-2)*N
     const unsigned bar_id = 1u + unsigned(slot);
     auto sync = [&]() {
         if (T == 32) __syncwarp();
         else slot_sync(bar_id, T);
     };
 
-    const DevSched& S = P.sched;
+    const DevSched& S = J.S;
     const float alpha = S.alpha;
     const int KW = (K + 31) / 32;
-    const int max_iters = P.max_iters;
+    const int max_iters = J.max_iters;
     const bool want_g = (S.stop_kind & 2) != 0;
 
     float L1[E];  // channel LLRs of the first group's positions
 
     while (true) {
-        if (tid == 0) ctl->frame = (long long)atomicAdd(P.counter, 1ull);
+        if (tid == 0) ctl->frame = (long long)atomicAdd(counter, 1ull);
         sync();
         const long long f = ctl->frame;
-        if (f >= P.B) break;
-        const float* llr_f = P.llr + size_t(f) * N;
+        if (f >= J.B) break;
+        const float* llr_f = J.llr + size_t(f) * N;
 
-        for (int i = tid; i < C::NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = tid; i < NW; i += T) dec[i] = 0u;
         if (tid == 0) {
             ctl->have_ev = 0;
@@ -267,7 +324,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
             ctl->ev_range = 0;
             ctl->ev_blk = -1;
             signed char none[16];
-            build_groups<LOGN, KB>(ctl, s_swz, false, 0, 0, 0, none);
+            build_groups<CL, KB>(ctl, s_swz, n, false, 0, 0, 0, none);
         }
         sync();
 
@@ -275,7 +332,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
         auto load_l1 = [&]() {
             if (!ctl->single_[0] && owner) {
                 const int cls = (ctl->local[0] && ((tid & ((1 << ctl->low) - 1)) == ctl->beta)) ? 1 : 0;
-                const int bs = sw(group_base<LOGN, KB>(ctl, 0, cls, tid));
+                const int bs = sw(group_base<CL, KB>(ctl, 0, cls, tid));
 #pragma unroll
                 for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + sw(bs ^ ctl->swoff[0][cls][e]));
             }
@@ -322,7 +379,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 }
                 if (owner) {
                     const int cls = (ctl->local[gi] && inb) ? 1 : 0;
-                    const int bs = sw(group_base<LOGN, KB>(ctl, gi, cls, tid));
+                    const int bs = sw(group_base<CL, KB>(ctl, gi, cls, tid));
                     int ph[E];
                     float x[E];
 #pragma unroll
@@ -361,7 +418,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
             float x[E];
             int phL[E];
             if (owner) {
-                const int bs = sw(group_base<LOGN, KB>(ctl, gL, clsL, tid));
+                const int bs = sw(group_base<CL, KB>(ctl, gL, clsL, tid));
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     phL[e] = bs ^ ctl->swoff[gL][clsL][e];
@@ -514,7 +571,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 }
                 if (owner) {
                     const int cls = (ctl->local[gi] && inb) ? 1 : 0;
-                    const int bs = sw(group_base<LOGN, KB>(ctl, gi, cls, tid));
+                    const int bs = sw(group_base<CL, KB>(ctl, gi, cls, tid));
                     int ph[E];
                     float y[E];
 #pragma unroll
@@ -560,7 +617,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                 if (S.stop_kind & 1) ok = res == 0;
                 if (want_g) {
                     if (warp == 0) {
-                        const bool gok = g_check<LOGN>(dec, xh, lane);
+                        const bool gok = LOGN ? g_check<(LOGN ? LOGN : 3)>(dec, xh, lane) : g_check_rt(dec, xh, lane, n);
                         if (lane == 0) ctl->g_ok = gok ? 1 : 0;
                     }
                     sync();
@@ -601,7 +658,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                             inc = qz > S.N_min ? qz : S.N_min;
                         }
                         ctl->next_inc = int(inc);
-                        build_groups<LOGN, KB>(ctl, s_swz, true, level, range, blk, order);
+                        build_groups<CL, KB>(ctl, s_swz, n, true, level, range, blk, order);
                     }
                     sync();
                     // resetVariableNodes: R at the interior levels of the previous
@@ -648,16 +705,25 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
                     bit = (dec[pos >> 5] >> (pos & 31)) & 1u;
                 }
                 const uint32_t word = __ballot_sync(0xffffffffu, bit);
-                if (lane == 0) P.bits[size_t(f) * KW + o] = word;
+                if (lane == 0) J.bits[size_t(f) * KW + o] = word;
             }
             sync();
             if (tid == 0) {
-                P.crc_ok[f] = ctl->crc_res == 0 ? 1 : 0;
-                P.iters[f] = used;
+                J.crc_ok[f] = ctl->crc_res == 0 ? 1 : 0;
+                J.iters[f] = used;
             }
             sync();
         }
     }
+}
+
+template <int LOGN, int KB, int FK>
+__global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_grouped_kernel(const __grid_constant__ BpParams P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    load_code_tables(P.code, smem);
+    __syncthreads();
+    grouped_frames<LOGN, KB, FK>(P.job, P.counter, smem, LOGN);
 }
 
 }  // namespace pcbp

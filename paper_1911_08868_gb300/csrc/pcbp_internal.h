@@ -38,6 +38,19 @@ struct DevSched {
     uint64_t seed, frame_base;
 };
 
+// One batch of frames of one code: the stage-grouped decoder body's inputs
+// and outputs (the frame counter is passed separately).
+struct FrameJob {
+    DevSched S;
+    const float* llr;
+    uint32_t* bits;
+    int32_t* iters;
+    uint8_t* crc_ok;
+    int64_t B;
+    int32_t max_iters;
+    int32_t K, r;
+};
+
 struct DevEvent {
     int32_t level, range;
     int64_t block;
@@ -57,6 +70,7 @@ struct BpParams {
     int32_t max_iters;
     int32_t slots;
     DevEvent events[PC_MAX_EVENTS];
+    FrameJob job;   // the same batch, as the stage-grouped kernel reads it
 };
 
 // Encoder tables: crc_pay[i] = x^(r + Kp - 1 - i) mod g for payload bit i.

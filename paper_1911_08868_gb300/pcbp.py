@@ -21,7 +21,9 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
-            "bp_decode_noalloc", "pc_status_string")
+            "bp_decode_noalloc", "bp_mixed_table_size", "bp_mixed_prepare", "bp_mixed_workspace_size",
+            "bp_decode_mixed", "pc_status_string")
+PC_MAX_BATCHES = 64
 PC_STATIC_SCRATCH_BYTES = 4096
 
 
@@ -48,6 +50,12 @@ class PcEvent(C.Structure):
     _fields_ = [("level", C.c_int32), ("range", C.c_int32), ("block", C.c_int64), ("order", C.c_int32 * 16)]
 
 
+class PcBatch(C.Structure):
+    _fields_ = [("code", C.POINTER(PcCode)), ("sched", PcSched), ("max_iters", C.c_int32), ("slots", C.c_int32),
+                ("B", C.c_int64), ("d_llr", C.c_void_p), ("d_bits", C.c_void_p), ("d_iters", C.c_void_p),
+                ("d_crc_ok", C.c_void_p)]
+
+
 _vp = C.c_void_p
 _lib.pc_construct.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.c_uint64, C.c_double, C.POINTER(PcCode)]
 _lib.pc_encode.argtypes = [C.POINTER(PcCode), _vp, _vp, C.c_int64, _vp]
@@ -58,6 +66,10 @@ _lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c
                                  C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
                                    _vp, _vp]
+_lib.bp_mixed_table_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
+_lib.bp_mixed_prepare.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, C.c_size_t]
+_lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
+_lib.bp_decode_mixed.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, _vp, _vp]
 _lib.pc_status_string.argtypes = [C.c_int]
 _lib.pc_status_string.restype = C.c_char_p
 
@@ -261,3 +273,68 @@ class HostDecoder:
             done.append((lo, hi))
         self.compute_stream.synchronize()
         return self.h_bits, self.h_iters, self.h_ok
+
+
+def bp_mixed_table_size(n_batches: int) -> int:
+    out = C.c_size_t(0)
+    _check("bp_mixed_table_size", _lib.bp_mixed_table_size(n_batches, C.byref(out)))
+    return out.value
+
+
+def bp_mixed_workspace_size(n_batches: int) -> int:
+    out = C.c_size_t(0)
+    _check("bp_mixed_workspace_size", _lib.bp_mixed_workspace_size(n_batches, C.byref(out)))
+    return out.value
+
+
+def bp_mixed_prepare(batches, h_table):
+    arr = (PcBatch * len(batches))(*batches)
+    _check("bp_mixed_prepare", _lib.bp_mixed_prepare(arr, len(batches), C.cast(h_table, C.c_void_p),
+                                                     C.sizeof(h_table)))
+
+
+def bp_decode_mixed(batches, d_table, workspace, stream=None):
+    arr = (PcBatch * len(batches))(*batches)
+    _check("bp_decode_mixed", _lib.bp_decode_mixed(arr, len(batches), _ptr(d_table), _ptr(workspace),
+                                                   _stream(stream)))
+
+
+class MixedDecoder:
+    """One persistent launch over several batches of different codes.
+
+    parts: list of (code, sched, max_iters, llr [B, N] CUDA float32 tensor, slots).  Output
+    tensors per batch are allocated here (`bits[i]`, `iters[i]`, `crc_ok[i]`); the device
+    descriptor table is prepared once and uploaded, so `__call__` only enqueues a memset and
+    one kernel (it can be captured in a CUDA graph after a first uncaptured call)."""
+
+    def __init__(self, parts, device="cuda"):
+        import torch
+
+        self.device = torch.device(device)
+        self.codes = [p[0] for p in parts]          # keep the host structs alive
+        self.llr = [p[3] for p in parts]
+        self.bits, self.iters, self.crc_ok, self.batches = [], [], [], []
+        for code, sch, max_iters, llr, slots in parts:
+            B = llr.shape[0]
+            bits = torch.empty((B, words_of(code.K)), dtype=torch.int32, device=self.device)
+            iters = torch.empty(B, dtype=torch.int32, device=self.device)
+            ok = torch.empty(B, dtype=torch.uint8, device=self.device)
+            self.bits.append(bits)
+            self.iters.append(iters)
+            self.crc_ok.append(ok)
+            b = PcBatch()
+            b.code = C.pointer(code)
+            b.sched = sch
+            b.max_iters, b.slots, b.B = max_iters, slots, B
+            b.d_llr, b.d_bits, b.d_iters, b.d_crc_ok = (llr.data_ptr(), bits.data_ptr(), iters.data_ptr(),
+                                                        ok.data_ptr())
+            self.batches.append(b)
+        nb = len(self.batches)
+        h = (C.c_char * max(bp_mixed_table_size(nb), 1))()
+        bp_mixed_prepare(self.batches, h)
+        self.table = torch.frombuffer(bytearray(h), dtype=torch.uint8).to(self.device)
+        self.workspace = torch.zeros(bp_mixed_workspace_size(nb), dtype=torch.uint8, device=self.device)
+
+    def __call__(self, stream=None):
+        bp_decode_mixed(self.batches, self.table, self.workspace, stream)
+        return self.bits, self.iters, self.crc_ok

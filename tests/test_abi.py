@@ -144,3 +144,34 @@ def test_pc_encode_validates(pcbp):
     assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), None, 4, None) == pcbp.PC_EINVAL
     assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), C.c_void_p(4096), -1, None) == pcbp.PC_EINVAL
     assert pcbp._lib.pc_encode(C.byref(code), C.c_void_p(4096), C.c_void_p(4096), 0, None) == pcbp.PC_OK
+
+
+@no_gpu_only
+def test_mixed_entry_points_validate_on_the_host(pcbp):
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    b = pcbp.PcBatch()
+    b.code = C.pointer(code)
+    b.sched = pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=5)
+    b.max_iters, b.slots, b.B = 10, 0, 4
+    b.d_llr = b.d_bits = b.d_iters = b.d_crc_ok = 4096
+    assert pcbp.bp_mixed_table_size(3) > 0 and pcbp.bp_mixed_workspace_size(3) >= 24
+    h = (C.c_char * pcbp.bp_mixed_table_size(1))()
+    bad = pcbp.PcBatch.from_buffer_copy(b)
+    bad.sched = pcbp.sched(mode=1, P_range=30, P_level=5, N_min=5, T0=5)
+    arr = (pcbp.PcBatch * 1)(bad)
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
+    nob = pcbp.PcBatch.from_buffer_copy(b)
+    nob.d_llr = None
+    arr = (pcbp.PcBatch * 1)(nob)
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
+    bx = pcbp.PcBatch.from_buffer_copy(b)
+    bx.sched = pcbp.sched(fkind=1)
+    arr = (pcbp.PcBatch * 1)(bx)
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EUNSUPPORTED
+    arr = (pcbp.PcBatch * 1)(b)
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), 8) == pcbp.PC_ENOMEM
+    assert pcbp._lib.bp_mixed_prepare(arr, 65, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_decode_mixed(arr, 0, None, None, None) == pcbp.PC_OK
+    assert pcbp._lib.bp_decode_mixed(arr, 1, None, C.c_void_p(4096), None) == pcbp.PC_EINVAL
+    bad_arr = (pcbp.PcBatch * 1)(bad)
+    assert pcbp._lib.bp_decode_mixed(bad_arr, 1, C.c_void_p(4096), C.c_void_p(4096), None) == pcbp.PC_EINVAL
