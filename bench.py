@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-wbp", action="store_true")
     return ap.parse_args()
 
 
@@ -296,6 +297,86 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
                         "max 300 it, CRC-8 (N<=256) / CRC-24"}
 
 
+def wbp_loss(logits, bits):
+    import torch
+
+    return torch.nn.functional.binary_cross_entropy_with_logits(-logits, bits.to(logits.dtype))
+
+
+def run_wbp(pcbp, inputs, dev, steps, warmup):
+    """Weighted BP fwd+bwd training steps/s at batch 4096 (Eb/N0 uniform on [1, 4] dB, weights
+    initialised to 0.9375, BCE on the information bits), and the largest relative error of the FP64
+    kernels' gradient against FP64 central finite differences at N = 16 and 64."""
+    import torch
+
+    out = {"batch": 4096, "steps_per_s": {}, "ms_per_step": {}}
+    B = 4096
+    for N in (256, 1024):
+        K = N // 2
+        code = pcbp.pc_construct(N, K)
+        n = N.bit_length() - 1
+        gen = torch.Generator(device=dev).manual_seed(N)
+        pay = inputs.payload_torch(gen, B, K, dev)
+        x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+        pcbp.pc_encode(code, pay, x)
+        ebn0 = (1.0 + 3.0 * torch.rand(B, generator=gen, device=dev, dtype=torch.float64)).cpu().numpy()
+        llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0, K, 0, N)).contiguous()
+        for T in (5, 10, 20):
+            w = torch.full((T, n, N // 2, 4), 0.9375, device=dev, requires_grad=True)
+
+            def step():
+                loss = wbp_loss(pcbp.wbp(llr, w, code, T), pay)
+                w.grad = None
+                loss.backward()
+
+            for _ in range(max(1, warmup)):
+                step()
+            torch.cuda.synchronize()
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            reps = max(1, min(steps, 5))
+            t0.record()
+            for _ in range(reps):
+                step()
+            t1.record()
+            torch.cuda.synchronize()
+            ms = t0.elapsed_time(t1) / reps
+            out["ms_per_step"][f"N{N}_T{T}"] = ms
+            out["steps_per_s"][f"N{N}_T{T}"] = 1e3 / ms
+    # gradient error of the FP64 kernels against central differences
+    errs = {}
+    for N, T in ((16, 3), (64, 3)):
+        K = N // 2
+        code = pcbp.pc_construct(N, K)
+        n = N.bit_length() - 1
+        gen = torch.Generator(device=dev).manual_seed(3 * N)
+        Bc = 8
+        pay = inputs.payload_torch(gen, Bc, K, dev)
+        x = torch.empty((Bc, N), dtype=torch.uint8, device=dev)
+        pcbp.pc_encode(code, pay, x)
+        llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(1.5, K, 0, N)).double().contiguous()
+        w = (0.9375 + 0.05 * torch.randn((T, n, N // 2, 4), generator=gen, device=dev, dtype=torch.float64))
+        w.requires_grad_()
+        wbp_loss(pcbp.wbp(llr, w, code, T), pay).backward()
+        g = w.grad.flatten()
+        idx = torch.argsort(g.abs(), descending=True)[:32]
+        eps, worst = 1e-6, 0.0
+        with torch.no_grad():
+            for i in idx.tolist():
+                wp = w.detach().clone().flatten()
+                wm = wp.clone()
+                wp[i] += eps
+                wm[i] -= eps
+                lp = wbp_loss(pcbp.wbp(llr, wp.view_as(w), code, T), pay)
+                lm = wbp_loss(pcbp.wbp(llr, wm.view_as(w), code, T), pay)
+                fd = float((lp - lm) / (2 * eps))
+                worst = max(worst, abs(fd - float(g[i])) / max(abs(fd), 1e-12))
+        errs[f"N{N}"] = worst
+    out["grad_max_rel_err_vs_fd64"] = errs
+    out["grad_check"] = "32 largest-gradient weights, central differences eps 1e-6, FP64 kernels, T=3, batch 8"
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -426,6 +507,9 @@ def run_ours(args):
                            "h2d_bytes_per_step": B * N * 4,
                            "d2h_bytes_per_step": B * (4 * math.ceil(K / 32) + 4 + 1), "steps": e_steps,
                            "chunks": hdec.chunks, "matches_device_run": same}
+
+    if rank == 0 and not args.no_wbp:
+        line["wbp"] = run_wbp(pcbp, inputs, dev, args.steps, args.warmup)
 
     if rank == 0 and not args.no_mixed:
         del dec

@@ -152,6 +152,43 @@ int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sch
                     int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
                     void* stream);
 
+/* ---- Weighted BP (a differentiable variant; the paper has no counterpart) -
+ * Unrolled round-trip BP on the original factor graph (Sec. II-B) with a
+ * learnable scale per f evaluation in place of the fixed min-sum scale:
+ * w[t][s][q][k] for iteration t < T, stage s < n (counted from the channel),
+ * processing element q < N/2 of that stage (q with a zero inserted at bit
+ * n-1-s is its top index) and k = 0 L_out1, 1 L_out2, 2 R_out1, 3 R_out2:
+ *   f_w(a, b) = w * sign(a) sign(b) * min(|a|, |b|).
+ * Frozen priors are +inf.  logits[b][k] = L at level n+1 of the k-th
+ * information position after T iterations (no CRC, no stop test, no
+ * permutation).  Gradients: the minimum takes the gradient (the first
+ * operand on ties), an infinite message receives none.
+ * FP32 entry points and _f64 twins (for gradient checks). */
+
+/* Number of weights, T * n * (N/2) * 4. */
+int wbp_weights_count(const pc_code* code, int32_t T, size_t* count);
+/* Number of checkpoint values, T * B * (n-1) * N (R of levels 2..n after
+ * t = 0..T-1 iterations). */
+int wbp_ckpt_count(const pc_code* code, int32_t T, int64_t B, size_t* count);
+/* Device workspace bytes of wbp_forward / wbp_backward (real_bytes 4 or 8). */
+int wbp_workspace_size(const pc_code* code, int32_t T, int64_t B, int32_t real_bytes, size_t* bytes);
+/* d_llr [B][N], d_w (wbp_weights_count), d_logits [B][K]; d_ckpt (nullable)
+ * receives the checkpoints wbp_backward needs. */
+int wbp_forward(const pc_code* code, const float* d_llr, const float* d_w, int32_t T, int64_t B,
+                float* d_logits, float* d_ckpt, void* d_workspace, void* stream);
+/* Given d_glogits = dLoss/dlogits [B][K]: d_gw += dLoss/dw (caller zeroes it
+ * for a fresh gradient); d_gllr (nullable) = dLoss/dllr [B][N].  Runs one
+ * launch per iteration, in reverse, each recomputing its iteration from the
+ * checkpoint. */
+int wbp_backward(const pc_code* code, const float* d_llr, const float* d_w, int32_t T, int64_t B,
+                 const float* d_ckpt, const float* d_glogits, float* d_gw, float* d_gllr,
+                 void* d_workspace, void* stream);
+int wbp_forward_f64(const pc_code* code, const double* d_llr, const double* d_w, int32_t T, int64_t B,
+                    double* d_logits, double* d_ckpt, void* d_workspace, void* stream);
+int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w, int32_t T, int64_t B,
+                     const double* d_ckpt, const double* d_glogits, double* d_gw, double* d_gllr,
+                     void* d_workspace, void* stream);
+
 /* ---- Mixed-length batched decoding (one persistent launch) ----------------
  * Several batches, each with its own code (any supported N and rate), schedule
  * and buffers, decoded by one launch whose CTAs drain the batches in order

@@ -58,7 +58,7 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         extra = [f"-DPCBP_KB={int(kb)}"] if kb else []
         jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
-    for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_mixed.cu"):
+    for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_mixed.cu", "wbp.cu"):
         extra = [f"-DPCBP_KB={int(kb)}"] if (kb and name == "bp_mixed.cu") else []
         obj = BUILD / (Path(name).stem + (f"_kb{int(kb)}" if extra else "") + ".o")
         jobs.append((obj, CSRC / name, [*common, *extra, "-c", str(CSRC / name), "-o", str(obj)]))

@@ -1,0 +1,486 @@
+// Weighted BP: a differentiable variant of the decoder (not in the paper).
+// Unrolled round-trip BP on the original factor graph (Sec. II-B) in which
+// each f evaluation has its own learnable scale w[t][s][q][k] (iteration t,
+// stage s, processing element q, and k = 0 L_out1, 1 L_out2, 2 R_out1,
+// 3 R_out2) in place of the fixed min-sum scale.  Forward keeps the R planes
+// at every iteration boundary as checkpoints; backward runs one launch per
+// iteration in reverse, recomputes that iteration from its checkpoint and
+// applies the adjoint of the R sweep then of the L sweep.
+//
+// Derivatives of f_w(a, b) = w sign(a) sign(b) min(|a|, |b|): with a the
+// minimum (|a| <= |b|: the first operand wins ties), df/da = w sign(b),
+// df/db = 0, df/dw = sign(a) sign(b) |a|; symmetrically otherwise.  Frozen
+// priors are +inf; an infinite message is never the minimum against a finite
+// one and receives no gradient, so updates with a zero upstream gradient are
+// skipped (never forming 0 * inf).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+
+#include "pcbp_internal.h"
+
+namespace pcbp {
+
+namespace {
+
+template <typename Real>
+struct WbpParams {
+    DevCode code;
+    const Real* llr;
+    const Real* w;
+    Real* logits;
+    Real* ckpt;          // [T][B][n-1][N], R of levels 2..n after t iterations (nullable in forward)
+    const Real* glogits;
+    Real* gw;            // [T][n][N/2][4], accumulated
+    Real* gllr;          // [B][N], accumulated over the launches (nullable)
+    const Real* gin;     // [B][n-1][N] gradient of R(t+1) levels 2..n (iteration it+1)
+    Real* gout;          // [B][n-1][N] gradient of R(t) levels 2..n
+    unsigned long long* counter;
+    int64_t B;
+    int32_t T;
+    int32_t it;          // backward: 0-based iteration handled by this launch
+    int32_t tps;         // threads per frame slot
+};
+
+template <typename Real>
+__device__ __forceinline__ Real inf_v();
+template <>
+__device__ __forceinline__ float inf_v<float>() { return __int_as_float(0x7f800000); }
+template <>
+__device__ __forceinline__ double inf_v<double>() { return __longlong_as_double(0x7ff0000000000000ll); }
+
+__device__ __forceinline__ float radd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double radd(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rmul(double a, double b) { return __dmul_rn(a, b); }
+
+template <typename Real>
+__device__ __forceinline__ Real sgn(Real v) { return v > Real(0) ? Real(1) : (v < Real(0) ? Real(-1) : Real(0)); }
+
+// w * sign(a) sign(b) min(|a|, |b|), the scale applied to the minimum first
+template <typename Real>
+__device__ __forceinline__ Real fw(Real a, Real b, Real w)
+{
+    const Real m = fabs(a) <= fabs(b) ? fabs(a) : fabs(b);
+    const Real v = rmul(w, m);
+    return (signbit(a) != signbit(b)) ? -v : v;
+}
+
+__device__ __forceinline__ int ins0(int q, int p) { return ((q >> p) << (p + 1)) | (q & ((1 << p) - 1)); }
+
+__device__ __forceinline__ void bar(unsigned id, unsigned count)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_constant__ WbpParams<Real> P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = P.code.n, N = 1 << n, NH = N / 2, K = P.code.K;
+    const int NW = N >= 32 ? N / 32 : 1;
+    const int tps = P.tps;
+    uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
+    int16_t* s_info = reinterpret_cast<int16_t*>(s_frozen + NW);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    __syncthreads();
+    const size_t tab = (size_t(NW) * 4 + size_t(K) * 2 + 15) & ~size_t(15);
+    const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
+    Real* L = reinterpret_cast<Real*>(smem + tab + size_t(slot) * size_t(2 * n) * N * sizeof(Real));  // levels 1..n+1
+    Real* R = L + size_t(n + 1) * N;                                                                 // levels 2..n
+    __shared__ long long s_frame[32];
+    const unsigned bid = 1u + unsigned(slot);
+    auto prior = [&](int j) { return ((s_frozen[j >> 5] >> (j & 31)) & 1u) ? inf_v<Real>() : Real(0); };
+
+    while (true) {
+        if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
+        bar(bid, tps);
+        const long long f = s_frame[slot];
+        if (f >= P.B) break;
+        for (int j = tid; j < N; j += tps) L[j] = P.llr[size_t(f) * N + j];
+        for (int j = tid; j < (n - 1) * N; j += tps) R[j] = Real(0);
+        if (P.ckpt)
+            for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = Real(0);
+        bar(bid, tps);
+        for (int it = 0; it < P.T; ++it) {
+            for (int s = 0; s < n; ++s) {
+                const int p = n - 1 - s;
+                for (int q = tid; q < NH; q += tps) {
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const Real lt = L[s * N + t], lb = L[s * N + b];
+                    const Real rt = s < n - 1 ? R[s * N + t] : prior(t);
+                    const Real rb = s < n - 1 ? R[s * N + b] : prior(b);
+                    const Real* w = P.w + ((size_t(it) * n + s) * NH + q) * 4;
+                    L[(s + 1) * N + t] = fw(lt, radd(lb, rb), w[0]);
+                    L[(s + 1) * N + b] = radd(fw(rt, lt, w[1]), lb);
+                }
+                bar(bid, tps);
+            }
+            if (it == P.T - 1) break;
+            for (int s = n - 1; s >= 1; --s) {
+                const int p = n - 1 - s;
+                for (int q = tid; q < NH; q += tps) {
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const Real lt = L[s * N + t], lb = L[s * N + b];
+                    const Real rt = s < n - 1 ? R[s * N + t] : prior(t);
+                    const Real rb = s < n - 1 ? R[s * N + b] : prior(b);
+                    const Real* w = P.w + ((size_t(it) * n + s) * NH + q) * 4;
+                    R[(s - 1) * N + t] = fw(rt, radd(lb, rb), w[2]);
+                    R[(s - 1) * N + b] = radd(fw(rt, lt, w[3]), rb);
+                }
+                bar(bid, tps);
+            }
+            if (P.ckpt) {
+                Real* dst = P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N;
+                for (int j = tid; j < (n - 1) * N; j += tps) dst[j] = R[j];
+                bar(bid, tps);
+            }
+        }
+        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[size_t(n) * N + s_info[k]];
+        bar(bid, tps);
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <typename Real>
+__global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_constant__ WbpParams<Real> P)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = P.code.n, N = 1 << n, NH = N / 2, K = P.code.K;
+    const int NW = N >= 32 ? N / 32 : 1;
+    const int tps = P.tps, it = P.it;
+    const bool last = it == P.T - 1;
+    uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
+    int16_t* s_info = reinterpret_cast<int16_t*>(s_frozen + NW);
+    const size_t tab = (size_t(NW) * 4 + size_t(K) * 2 + 15) & ~size_t(15);
+    Real* dw = reinterpret_cast<Real*>(smem + tab);                                   // [n][NH][4]
+    const size_t dw_bytes = (size_t(n) * NH * 4 * sizeof(Real) + 15) & ~size_t(15);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    for (int i = threadIdx.x; i < n * NH * 4; i += blockDim.x) dw[i] = Real(0);
+    __syncthreads();
+    const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
+    const size_t slot_reals = size_t(3 * n + 3) * N;
+    Real* L = reinterpret_cast<Real*>(smem + tab + dw_bytes) + size_t(slot) * slot_reals;   // levels 1..n+1
+    Real* Rt = L + size_t(n + 1) * N;                                                        // R(it) levels 2..n
+    Real* gL = Rt + size_t(n - 1) * N;                                                       // levels 1..n+1
+    Real* gA = gL + size_t(n + 1) * N;
+    Real* gB = gA + N;
+    __shared__ long long s_frame[32];
+    const unsigned bid = 1u + unsigned(slot);
+    auto prior = [&](int j) { return ((s_frozen[j >> 5] >> (j & 31)) & 1u) ? inf_v<Real>() : Real(0); };
+    const Real* wt = P.w + size_t(it) * n * NH * 4;
+
+    while (true) {
+        if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
+        bar(bid, tps);
+        const long long f = s_frame[slot];
+        if (f >= P.B) break;
+        const Real* Rp = P.ckpt + (size_t(it) * P.B + size_t(f)) * (n - 1) * N;   // R(it) before this iteration
+        auto rprev = [&](int s, int j) { return s < n - 1 ? Rp[size_t(s) * N + j] : prior(j); };   // level s+2
+        for (int j = tid; j < N; j += tps) L[j] = P.llr[size_t(f) * N + j];
+        for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = Real(0);
+        for (int j = tid; j < N; j += tps) gA[j] = gB[j] = Real(0);
+        bar(bid, tps);
+        // forward recomputation of iteration it
+        for (int s = 0; s < n; ++s) {
+            const int p = n - 1 - s;
+            for (int q = tid; q < NH; q += tps) {
+                const int t = ins0(q, p), b = t | (1 << p);
+                const Real lt = L[s * N + t], lb = L[s * N + b];
+                const Real rt = rprev(s, t), rb = rprev(s, b);
+                const Real* w = wt + (size_t(s) * NH + q) * 4;
+                L[(s + 1) * N + t] = fw(lt, radd(lb, rb), w[0]);
+                L[(s + 1) * N + b] = radd(fw(rt, lt, w[1]), lb);
+            }
+            bar(bid, tps);
+        }
+        if (!last) {
+            for (int s = n - 1; s >= 1; --s) {
+                const int p = n - 1 - s;
+                for (int q = tid; q < NH; q += tps) {
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const Real lt = L[s * N + t], lb = L[s * N + b];
+                    const Real rt = s < n - 1 ? Rt[s * N + t] : prior(t);
+                    const Real rb = s < n - 1 ? Rt[s * N + b] : prior(b);
+                    const Real* w = wt + (size_t(s) * NH + q) * 4;
+                    Rt[(s - 1) * N + t] = fw(rt, radd(lb, rb), w[2]);
+                    Rt[(s - 1) * N + b] = radd(fw(rt, lt, w[3]), rb);
+                }
+                bar(bid, tps);
+            }
+        } else {
+            for (int k = tid; k < K; k += tps) gL[size_t(n) * N + s_info[k]] = P.glogits[size_t(f) * K + k];
+            bar(bid, tps);
+        }
+        // adjoint of the R sweep: stage s makes R level s+1 from R level s+2 and L level s+1
+        if (!last) {
+            const Real* gin = P.gin + size_t(f) * (n - 1) * N;
+            for (int s = 1; s <= n - 1; ++s) {
+                const int p = n - 1 - s;
+                for (int q = tid; q < NH; q += tps) {
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const Real gt = radd(gin[size_t(s - 1) * N + t], gA[t]);   // gradient of R level s+1
+                    const Real gb = radd(gin[size_t(s - 1) * N + b], gA[b]);
+                    const Real a = s < n - 1 ? Rt[s * N + t] : prior(t);       // R level s+2
+                    const Real rb = s < n - 1 ? Rt[s * N + b] : prior(b);
+                    const Real lt = L[s * N + t], lb = L[s * N + b];
+                    const Real* w = wt + (size_t(s) * NH + q) * 4;
+                    Real* d = dw + (size_t(s) * NH + q) * 4;
+                    Real ct = Real(0), cb = Real(0);
+                    if (gt != Real(0)) {                                        // R_out1 = f(a, lb + rb; w2)
+                        const Real c = radd(lb, rb);
+                        const bool amin = fabs(a) <= fabs(c);
+                        const Real m = amin ? fabs(a) : fabs(c);
+                        atomicAdd(d + 2, rmul(gt, sgn(a) * sgn(c) * m));
+                        if (amin) {
+                            ct = radd(ct, rmul(rmul(gt, w[2]), sgn(c)));
+                        } else {
+                            const Real gc = rmul(rmul(gt, w[2]), sgn(a));
+                            gL[s * N + b] = radd(gL[s * N + b], gc);
+                            cb = radd(cb, gc);
+                        }
+                    }
+                    if (gb != Real(0)) {                                        // R_out2 = f(a, lt; w3) + rb
+                        cb = radd(cb, gb);
+                        const bool amin = fabs(a) <= fabs(lt);
+                        const Real m = amin ? fabs(a) : fabs(lt);
+                        atomicAdd(d + 3, rmul(gb, sgn(a) * sgn(lt) * m));
+                        if (amin) ct = radd(ct, rmul(rmul(gb, w[3]), sgn(lt)));
+                        else gL[s * N + t] = radd(gL[s * N + t], rmul(rmul(gb, w[3]), sgn(a)));
+                    }
+                    gB[t] = ct;                                                 // contributions to R level s+2
+                    gB[b] = cb;
+                }
+                bar(bid, tps);
+                Real* tmp = gA; gA = gB; gB = tmp;
+            }
+        }
+        // adjoint of the L sweep: stage s makes L level s+2 from L level s+1 and R(it) level s+2
+        Real* gout = P.gout + size_t(f) * (n - 1) * N;
+        for (int s = n - 1; s >= 0; --s) {
+            const int p = n - 1 - s;
+            for (int q = tid; q < NH; q += tps) {
+                const int t = ins0(q, p), b = t | (1 << p);
+                const Real gt = gL[(s + 1) * N + t], gb = gL[(s + 1) * N + b];
+                const Real a = L[s * N + t], lb = L[s * N + b];
+                const Real rt = rprev(s, t), rb = rprev(s, b);
+                const Real* w = wt + (size_t(s) * NH + q) * 4;
+                Real* d = dw + (size_t(s) * NH + q) * 4;
+                Real gRt = Real(0), gRb = Real(0);
+                Real gat = gL[s * N + t], gab = gL[s * N + b];
+                if (gt != Real(0)) {                                            // L_out1 = f(a, lb + rb; w0)
+                    const Real c = radd(lb, rb);
+                    const bool amin = fabs(a) <= fabs(c);
+                    const Real m = amin ? fabs(a) : fabs(c);
+                    atomicAdd(d + 0, rmul(gt, sgn(a) * sgn(c) * m));
+                    if (amin) {
+                        gat = radd(gat, rmul(rmul(gt, w[0]), sgn(c)));
+                    } else {
+                        const Real gc = rmul(rmul(gt, w[0]), sgn(a));
+                        gab = radd(gab, gc);
+                        gRb = radd(gRb, gc);
+                    }
+                }
+                if (gb != Real(0)) {                                            // L_out2 = f(rt, a; w1) + lb
+                    gab = radd(gab, gb);
+                    const bool rmin = fabs(rt) <= fabs(a);
+                    const Real m = rmin ? fabs(rt) : fabs(a);
+                    atomicAdd(d + 1, rmul(gb, sgn(rt) * sgn(a) * m));
+                    if (rmin) gRt = radd(gRt, rmul(rmul(gb, w[1]), sgn(a)));
+                    else gat = radd(gat, rmul(rmul(gb, w[1]), sgn(rt)));
+                }
+                gL[s * N + t] = gat;
+                gL[s * N + b] = gab;
+                if (s < n - 1) {
+                    gout[size_t(s) * N + t] = gRt;
+                    gout[size_t(s) * N + b] = gRb;
+                }
+            }
+            bar(bid, tps);
+        }
+        if (P.gllr)
+            for (int j = tid; j < N; j += tps) P.gllr[size_t(f) * N + j] = radd(P.gllr[size_t(f) * N + j], gL[j]);
+        bar(bid, tps);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n * NH * 4; i += blockDim.x)
+        if (dw[i] != Real(0)) atomicAdd(P.gw + size_t(it) * n * NH * 4 + i, dw[i]);
+}
+
+struct Geo {
+    int tps, slots, grid;
+    size_t smem;
+};
+
+int wbp_geometry(const pc_code* c, int64_t B, size_t real_bytes, bool backward, Geo* g)
+{
+    int dev = 0, sms = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PC_ECUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PC_ECUDA;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return PC_ECUDA;
+    optin -= 1024;   // static shared variables of the kernels
+    const int N = c->N, n = c->n;
+    const int NW = N >= 32 ? N / 32 : 1;
+    const size_t tab = (size_t(NW) * 4 + size_t(c->K) * 2 + 15) & ~size_t(15);
+    const size_t fixed = tab + (backward ? ((size_t(n) * (N / 2) * 4 * real_bytes + 15) & ~size_t(15)) : 0);
+    const size_t slot = (backward ? size_t(3 * n + 3) : size_t(2 * n)) * N * real_bytes;
+    g->tps = std::max(32, std::min(512, N / 2));
+    if (fixed + slot > size_t(optin)) return PC_EUNSUPPORTED;
+    int slots = int((size_t(optin) - fixed) / slot);
+    slots = std::max(1, std::min({slots, 15, 1024 / g->tps}));
+    g->slots = slots;
+    g->smem = fixed + size_t(slots) * slot;
+    g->grid = int(std::min<int64_t>(int64_t(sms), (B + slots - 1) / slots));
+    return PC_OK;
+}
+
+int validate_common(const pc_code* c, int32_t T, int64_t B)
+{
+    int rc = validate_code(c);
+    if (rc != PC_OK) return rc;
+    if (T < 1 || T > 1024 || B < 0) return PC_EINVAL;
+    return PC_OK;
+}
+
+size_t workspace_bytes(const pc_code* c, int64_t B, size_t real_bytes)
+{
+    return 256 + 2 * size_t(B) * size_t(c->n - 1) * size_t(c->N) * real_bytes;
+}
+
+template <typename Real>
+int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, int64_t B, Real* logits, Real* ckpt,
+                 void* ws, void* stream)
+{
+    int rc = validate_common(c, T, B);
+    if (rc != PC_OK) return rc;
+    if (B == 0) return PC_OK;
+    if (!llr || !w || !logits || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
+    Geo g;
+    rc = wbp_geometry(c, B, sizeof(Real), false, &g);
+    if (rc != PC_OK) return rc;
+    std::unique_ptr<WbpParams<Real>> P(new WbpParams<Real>);
+    std::memset(P.get(), 0, sizeof(WbpParams<Real>));
+    build_dev_code(c, &P->code);
+    P->llr = llr;
+    P->w = w;
+    P->logits = logits;
+    P->ckpt = ckpt;
+    P->counter = static_cast<unsigned long long*>(ws);
+    P->B = B;
+    P->T = T;
+    P->tps = g.tps;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
+    if (cudaFuncSetAttribute(wbp_forward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
+        cudaSuccess)
+        return PC_ECUDA;
+    wbp_forward_kernel<Real><<<g.grid, g.slots * g.tps, g.smem, st>>>(*P);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
+}
+
+template <typename Real>
+int backward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, int64_t B, const Real* ckpt,
+                  const Real* glogits, Real* gw, Real* gllr, void* ws, void* stream)
+{
+    int rc = validate_common(c, T, B);
+    if (rc != PC_OK) return rc;
+    if (B == 0) return PC_OK;
+    if (!llr || !w || !ckpt || !glogits || !gw || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
+    Geo g;
+    rc = wbp_geometry(c, B, sizeof(Real), true, &g);
+    if (rc != PC_OK) return rc;
+    std::unique_ptr<WbpParams<Real>> P(new WbpParams<Real>);
+    std::memset(P.get(), 0, sizeof(WbpParams<Real>));
+    build_dev_code(c, &P->code);
+    P->llr = llr;
+    P->w = w;
+    P->ckpt = const_cast<Real*>(ckpt);
+    P->glogits = glogits;
+    P->gw = gw;
+    P->gllr = gllr;
+    P->counter = static_cast<unsigned long long*>(ws);
+    P->B = B;
+    P->T = T;
+    P->tps = g.tps;
+    Real* state[2];
+    state[0] = reinterpret_cast<Real*>(static_cast<unsigned char*>(ws) + 256);
+    state[1] = state[0] + size_t(B) * size_t(c->n - 1) * size_t(c->N);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (gllr && cudaMemsetAsync(gllr, 0, size_t(B) * c->N * sizeof(Real), st) != cudaSuccess) return PC_ECUDA;
+    if (cudaFuncSetAttribute(wbp_backward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
+        cudaSuccess)
+        return PC_ECUDA;
+    for (int it = T - 1; it >= 0; --it) {
+        P->it = it;
+        P->gin = state[(T - 1 - it) & 1];      // written by the launch of iteration it+1 (unused at it = T-1)
+        P->gout = state[(T - it) & 1];
+        if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
+        wbp_backward_kernel<Real><<<g.grid, g.slots * g.tps, g.smem, st>>>(*P);
+        if (cudaGetLastError() != cudaSuccess) return PC_ECUDA;
+    }
+    return PC_OK;
+}
+
+}  // namespace
+
+}  // namespace pcbp
+
+using namespace pcbp;
+
+extern "C" int wbp_weights_count(const pc_code* code, int32_t T, size_t* count)
+{
+    int rc = validate_common(code, T, 0);
+    if (rc != PC_OK) return rc;
+    if (!count) return PC_EINVAL;
+    *count = size_t(T) * code->n * (code->N / 2) * 4;
+    return PC_OK;
+}
+
+extern "C" int wbp_ckpt_count(const pc_code* code, int32_t T, int64_t B, size_t* count)
+{
+    int rc = validate_common(code, T, B);
+    if (rc != PC_OK) return rc;
+    if (!count) return PC_EINVAL;
+    *count = size_t(T) * size_t(B) * size_t(code->n - 1) * size_t(code->N);
+    return PC_OK;
+}
+
+extern "C" int wbp_workspace_size(const pc_code* code, int32_t T, int64_t B, int32_t real_bytes, size_t* bytes)
+{
+    int rc = validate_common(code, T, B);
+    if (rc != PC_OK) return rc;
+    if (!bytes || (real_bytes != 4 && real_bytes != 8)) return PC_EINVAL;
+    *bytes = workspace_bytes(code, B, size_t(real_bytes));
+    return PC_OK;
+}
+
+extern "C" int wbp_forward(const pc_code* code, const float* d_llr, const float* d_w, int32_t T, int64_t B,
+                           float* d_logits, float* d_ckpt, void* d_workspace, void* stream)
+{
+    return forward_impl<float>(code, d_llr, d_w, T, B, d_logits, d_ckpt, d_workspace, stream);
+}
+
+extern "C" int wbp_backward(const pc_code* code, const float* d_llr, const float* d_w, int32_t T, int64_t B,
+                            const float* d_ckpt, const float* d_glogits, float* d_gw, float* d_gllr,
+                            void* d_workspace, void* stream)
+{
+    return backward_impl<float>(code, d_llr, d_w, T, B, d_ckpt, d_glogits, d_gw, d_gllr, d_workspace, stream);
+}
+
+extern "C" int wbp_forward_f64(const pc_code* code, const double* d_llr, const double* d_w, int32_t T, int64_t B,
+                               double* d_logits, double* d_ckpt, void* d_workspace, void* stream)
+{
+    return forward_impl<double>(code, d_llr, d_w, T, B, d_logits, d_ckpt, d_workspace, stream);
+}
+
+extern "C" int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w, int32_t T, int64_t B,
+                                const double* d_ckpt, const double* d_glogits, double* d_gw, double* d_gllr,
+                                void* d_workspace, void* stream)
+{
+    return backward_impl<double>(code, d_llr, d_w, T, B, d_ckpt, d_glogits, d_gw, d_gllr, d_workspace, stream);
+}

@@ -22,7 +22,8 @@ PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
             "bp_decode_noalloc", "bp_mixed_table_size", "bp_mixed_prepare", "bp_mixed_workspace_size",
-            "bp_decode_mixed", "pc_status_string")
+            "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
+            "wbp_backward", "wbp_forward_f64", "wbp_backward_f64", "pc_status_string")
 PC_MAX_BATCHES = 64
 PC_STATIC_SCRATCH_BYTES = 4096
 
@@ -70,6 +71,13 @@ _lib.bp_mixed_table_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_mixed_prepare.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, C.c_size_t]
 _lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_decode_mixed.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, _vp, _vp]
+_lib.wbp_weights_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_size_t)]
+_lib.wbp_ckpt_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]
+_lib.wbp_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
+for _nm in ("wbp_forward", "wbp_forward_f64"):
+    getattr(_lib, _nm).argtypes = [C.POINTER(PcCode), _vp, _vp, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp]
+for _nm in ("wbp_backward", "wbp_backward_f64"):
+    getattr(_lib, _nm).argtypes = [C.POINTER(PcCode), _vp, _vp, C.c_int32, C.c_int64, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.pc_status_string.argtypes = [C.c_int]
 _lib.pc_status_string.restype = C.c_char_p
 
@@ -338,3 +346,76 @@ class MixedDecoder:
     def __call__(self, stream=None):
         bp_decode_mixed(self.batches, self.table, self.workspace, stream)
         return self.bits, self.iters, self.crc_ok
+
+
+def wbp_weights_count(code: PcCode, T: int) -> int:
+    out = C.c_size_t(0)
+    _check("wbp_weights_count", _lib.wbp_weights_count(C.byref(code), T, C.byref(out)))
+    return out.value
+
+
+def wbp_ckpt_count(code: PcCode, T: int, B: int) -> int:
+    out = C.c_size_t(0)
+    _check("wbp_ckpt_count", _lib.wbp_ckpt_count(C.byref(code), T, B, C.byref(out)))
+    return out.value
+
+
+def wbp_workspace_size(code: PcCode, T: int, B: int, real_bytes: int) -> int:
+    out = C.c_size_t(0)
+    _check("wbp_workspace_size", _lib.wbp_workspace_size(C.byref(code), T, B, real_bytes, C.byref(out)))
+    return out.value
+
+
+def wbp_forward(code: PcCode, llr, w, T: int, logits, ckpt, workspace, stream=None):
+    fn = "wbp_forward_f64" if llr.element_size() == 8 else "wbp_forward"
+    _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(logits), _ptr(ckpt),
+                                 _ptr(workspace), _stream(stream)))
+
+
+def wbp_backward(code: PcCode, llr, w, T: int, ckpt, glogits, gw, gllr, workspace, stream=None):
+    fn = "wbp_backward_f64" if llr.element_size() == 8 else "wbp_backward"
+    _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(ckpt), _ptr(glogits),
+                                 _ptr(gw), _ptr(gllr), _ptr(workspace), _stream(stream)))
+
+
+def _wbp_function():
+    import torch
+
+    class WBPFunction(torch.autograd.Function):
+        """logits = weighted BP(llr, w): forward and hand-written backward kernels."""
+
+        @staticmethod
+        def forward(ctx, llr, w, code, T):
+            llr = llr.contiguous()
+            w = w.contiguous()
+            B = llr.shape[0]
+            logits = torch.empty((B, code.K), dtype=llr.dtype, device=llr.device)
+            ckpt = torch.empty(wbp_ckpt_count(code, T, B), dtype=llr.dtype, device=llr.device)
+            ws = torch.empty(wbp_workspace_size(code, T, B, llr.element_size()), dtype=torch.uint8,
+                             device=llr.device)
+            wbp_forward(code, llr, w, T, logits, ckpt, ws)
+            ctx.save_for_backward(llr, w, ckpt)
+            ctx.code, ctx.T, ctx.ws = code, T, ws
+            return logits
+
+        @staticmethod
+        def backward(ctx, glogits):
+            llr, w, ckpt = ctx.saved_tensors
+            gw = torch.zeros_like(w)
+            gllr = torch.empty_like(llr) if ctx.needs_input_grad[0] else None
+            wbp_backward(ctx.code, llr, w, ctx.T, ckpt, glogits.contiguous(), gw, gllr, ctx.ws)
+            return gllr, gw, None, None
+
+    return WBPFunction
+
+
+
+
+def wbp(llr, w, code: PcCode, T: int):
+    """Differentiable weighted BP: logits [B, K] from llr [B, N] and w [T, n, N/2, 4] (CUDA tensors)."""
+    global _WBP
+    try:
+        fn = _WBP
+    except NameError:
+        fn = _WBP = _wbp_function()
+    return fn.apply(llr, w, code, T)
