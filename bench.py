@@ -77,7 +77,7 @@ def measured_peaks():
 
 def profiled_traffic(sha: str):
     """DRAM bytes per full launch from the committed ncu summary, if it was taken on this kernel source."""
-    p = ROOT / "profiles" / "bp_decode_n1024_pp_s4t10.md"
+    p = ROOT / "profiles" / "bp_decode_grouped_n1024_pp_s4t10.md"
     if not p.exists():
         return None
     vals = {}
@@ -397,9 +397,12 @@ def run_ours(args):
         dist.barrier()
     from paper_1911_08868_gb300 import inputs, pcbp
 
-    B = args.frames
+    from paper_1911_08868_gb300.shard import reduce_counters, shard_range
+
+    B = args.frames                       # frames per rank (weak scaling)
+    lo, hi = shard_range(world * B, world, rank)
     code = pcbp.pc_construct(N, K, R_CRC, POLY)
-    sch = pcbp.sched(**SCHED, frame_base=rank * B)
+    sch = pcbp.sched(**SCHED, frame_base=lo)
     gen = torch.Generator(device=dev).manual_seed(1234 + rank)
     pay = inputs.payload_torch(gen, B, K - R_CRC, dev)
     x = torch.empty((B, N), dtype=torch.uint8, device=dev)
@@ -442,8 +445,10 @@ def run_ours(args):
     ok = dec.crc_ok.to(torch.int64)
     got = pcbp.unpack_bits(dec.bits, K)[:, : K - R_CRC]
     frame_err = (got != pay).any(dim=1)
-    errors = int(frame_err.sum().item())
-    mean_iters = float(iters.float().mean().item())
+    job = reduce_counters({"frames": B, "frame_errors": int(frame_err.sum().item()),
+                           "bit_errors": int((got != pay).sum().item()), "iterations": int(iters.sum().item())})
+    errors = job["frame_errors"]
+    mean_iters = job["iterations"] / job["frames"]
     half_sweeps = int((2 * iters - ok).sum().item())   # a CRC stop skips that iteration's R sweep
     info_bits = B * (K - R_CRC)
     value = world * info_bits * args.steps / (total_ms / 1e3) / 1e9
@@ -479,7 +484,8 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (%.1f GB of LLRs per step)" % (B * N * 4 / 1e9),
                        "parallelism": f"frame shards x{world}"},
             "frames_per_s": world * B * args.steps / (total_ms / 1e3),
-            "mean_iters": mean_iters, "fer": errors / B, "fer_ci95": wilson(errors, B),
+            "mean_iters": mean_iters, "fer": errors / job["frames"], "fer_ci95": wilson(errors, job["frames"]),
+            "ber": job["bit_errors"] / (job["frames"] * (K - R_CRC)),
             "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
         }
 
