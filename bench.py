@@ -65,7 +65,7 @@ def dist_env():
 
 def kernel_sha() -> str:
     h = hashlib.sha256()
-    for name in ("bp_kernel.cuh", "bp_kernel2.cuh", "bp_inst2.cu"):   # the bp_decode kernel's source
+    for name in ("bp_kernel.cuh", "bp_kernel2.cuh", "bp_kernel3.cuh", "bp_inst3.cu"):   # the N = 1024 bp_decode kernel
         h.update((ROOT / "paper_1911_08868_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:12]
 
@@ -77,7 +77,7 @@ def measured_peaks():
 
 def profiled_traffic(sha: str):
     """DRAM bytes per full launch from the committed ncu summary, if it was taken on this kernel source."""
-    p = ROOT / "profiles" / "bp_decode_grouped_n1024_pp_s4t10.md"
+    p = ROOT / "profiles" / "bp_decode_tmem_n1024_pp_s4t10.md"
     if not p.exists():
         return None
     vals = {}

@@ -1,7 +1,9 @@
 """Builds libpcbp.so in-tree with nvcc for sm_103a (no cmake, no setuptools).
 
-The decoder kernels are instantiated once per code length (n = 3..11) from
-``csrc/bp_inst.cu``; those translation units compile in parallel.  Objects go
+The decoder kernels are instantiated once per code length from
+``csrc/bp_inst.cu`` and ``csrc/bp_inst2.cu`` (n = 3..11) and
+``csrc/bp_inst3.cu`` (n = 8..11); those translation units compile in
+parallel.  Objects go
 to ``_build/`` at the repository root; the library is written next to this
 file.  A rebuild only recompiles objects older than their sources or any
 header.
@@ -23,6 +25,7 @@ LIB = PKG / "libpcbp.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 LOGNS = range(3, 12)
+LOGNS_TMEM = range(8, 12)    # the TMEM kernel needs 2^KB positions on every lane of a warp
 
 
 def _nvcc() -> str:
@@ -58,6 +61,10 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         extra = [f"-DPCBP_KB={int(kb)}"] if kb else []
         jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
+    for n in LOGNS_TMEM:
+        obj = BUILD / f"bp_inst3_{n}.o"
+        jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst3.cu"),
+                                                 "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_mixed.cu", "wbp.cu"):
         extra = [f"-DPCBP_KB={int(kb)}"] if (kb and name == "bp_mixed.cu") else []
         obj = BUILD / (Path(name).stem + (f"_kb{int(kb)}" if extra else "") + ".o")

@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 
@@ -15,6 +16,7 @@ namespace {
 struct DeviceInfo {
     int sms = 0;
     int smem_optin = 0;
+    int smem_per_sm = 0;
 };
 
 int device_info(DeviceInfo* out)
@@ -29,6 +31,8 @@ int device_info(DeviceInfo* out)
     DeviceInfo d;
     if (cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return PC_ECUDA;
     if (cudaDeviceGetAttribute(&d.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return PC_ECUDA;
+    if (cudaDeviceGetAttribute(&d.smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess)
         return PC_ECUDA;
     if (dev < 64) cache[dev] = d;
     *out = d;
@@ -118,6 +122,45 @@ cudaError_t launch2_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cu
     return e;
 }
 
+void shape3_of(int n, int* T, size_t* slot, int* max_slots)
+{
+    switch (n) {
+        case 8: bp3_shape_8(T, slot, max_slots); break;
+        case 9: bp3_shape_9(T, slot, max_slots); break;
+        case 10: bp3_shape_10(T, slot, max_slots); break;
+        default: bp3_shape_11(T, slot, max_slots); break;
+    }
+}
+
+int occupancy3_of(int n, const LaunchGeom& g, int fk)
+{
+    switch (n) {
+        case 8: return bp3_occupancy_8(g, fk);
+        case 9: return bp3_occupancy_9(g, fk);
+        case 10: return bp3_occupancy_10(g, fk);
+        default: return bp3_occupancy_11(g, fk);
+    }
+}
+
+cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st)
+{
+    switch (n) {
+        case 8: return bp3_launch_8(P, g, fk, st);
+        case 9: return bp3_launch_9(P, g, fk, st);
+        case 10: return bp3_launch_10(P, g, fk, st);
+        default: return bp3_launch_11(P, g, fk, st);
+    }
+}
+
+// The TMEM kernel serves n = 8..11 unless PCBP_DECODER=grouped selects the
+// shared-memory-only kernel (both give identical outputs).
+bool use_tmem_kernel(int n)
+{
+    if (n < 8 || n > 11) return false;
+    const char* v = std::getenv("PCBP_DECODER");
+    return !(v && std::strcmp(v, "grouped") == 0);
+}
+
 size_t table_bytes(int N, int r, int K)
 {
     const size_t nw = size_t(N >= 32 ? N / 32 : 1);
@@ -170,6 +213,32 @@ int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
     if (occ < 1) return PC_EUNSUPPORTED;
     const int64_t need = (B + slots - 1) / slots;
     g->grid = int(std::min<int64_t>(need, int64_t(di.sms) * occ));
+    return PC_OK;
+}
+
+// TMEM kernel: slots as for the stage-grouped kernel, then at least half an
+// SM's shared memory per CTA, so that one CTA per SM holds all 512 TMEM
+// columns and no allocation ever waits for another CTA.
+int plan_launch3(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
+{
+    DeviceInfo di;
+    int rc = device_info(&di);
+    if (rc != PC_OK) return rc;
+    int T = 0, max_slots = 0;
+    size_t slot = 0;
+    shape3_of(c->n, &T, &slot, &max_slots);
+    const size_t tab = table_bytes(c->N, c->crc_len, c->K) + 64;   // + the 64-byte swizzle table
+    if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
+    int slots = int((size_t(di.smem_optin) - tab) / slot);
+    slots = std::max(1, std::min(slots, max_slots));
+    g->slots = slots;
+    g->smem = std::max(tab + size_t(slots) * slot, size_t(di.smem_per_sm) / 2 + 1024);
+    if (g->smem > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
+    g->grid = 1;
+    const int occ = occupancy3_of(c->n, *g, fk);
+    if (occ != 1) return PC_EUNSUPPORTED;
+    const int64_t need = (B + slots - 1) / slots;
+    g->grid = int(std::min<int64_t>(need, int64_t(di.sms)));
     return PC_OK;
 }
 
@@ -243,13 +312,16 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     P->job.r = code->crc_len;
 
     LaunchGeom g;
-    rc = trace ? plan_launch(code, B, trace, sched->fkind, &g) : plan_launch2(code, B, sched->fkind, &g);
+    const bool tmem = !trace && use_tmem_kernel(code->n);
+    rc = trace ? plan_launch(code, B, trace, sched->fkind, &g)
+               : (tmem ? plan_launch3(code, B, sched->fkind, &g) : plan_launch2(code, B, sched->fkind, &g));
     if (rc != PC_OK) return rc;
     P->slots = g.slots;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
-    const cudaError_t e = trace ? launch_of(code->n, *P, g, true, sched->fkind, st)
-                                : launch2_of(code->n, *P, g, sched->fkind, st);
+    const cudaError_t e = trace  ? launch_of(code->n, *P, g, true, sched->fkind, st)
+                          : tmem ? launch3_of(code->n, *P, g, sched->fkind, st)
+                                 : launch2_of(code->n, *P, g, sched->fkind, st);
     if (e != cudaSuccess) return PC_ECUDA;
     return PC_OK;
 }

@@ -1,0 +1,68 @@
+// Instantiates the TMEM-resident stage-grouped decoder kernel for one code
+// length, 2^PCBP_LOGN (compiled once per n = 8..11: every lane of a warp owns
+// 2^KB positions from N = 256 on).
+#include "bp_kernel3.cuh"
+#include "bp_launch.h"
+
+#ifndef PCBP_LOGN
+#error "PCBP_LOGN must be defined"
+#endif
+
+#define PCBP_CAT2(a, b) a##b
+#define PCBP_CAT(a, b) PCBP_CAT2(a, b)
+
+namespace pcbp {
+
+namespace {
+#ifndef PCBP_KB3
+#define PCBP_KB3 3
+#endif
+constexpr int KB = PCBP_KB3;   // 2^KB positions per thread
+using Geo = G3<PCBP_LOGN, KB>;
+
+template <int FK>
+cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st)
+{
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
+    if (e != cudaSuccess) return e;
+    kern<<<g.grid, g.slots * Geo::T, g.smem, st>>>(P);
+    return cudaGetLastError();
+}
+
+template <int FK>
+int occupancy(const LaunchGeom& g)
+{
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) != cudaSuccess)
+        return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, kern, g.slots * Geo::T, g.smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+}  // namespace
+
+void PCBP_CAT(bp3_shape_, PCBP_LOGN)(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out)
+{
+    *threads_per_slot_out = Geo::T;
+    *slot_bytes_out = align16(sizeof(Ctl3<PCBP_LOGN, KB>)) + align16(2 * Geo::NW * 4) +
+                      size_t(2 * Geo::NPL) * Geo::N * 4;
+    int slots = tmem_max_threads<PCBP_LOGN>() / Geo::T;
+    const int by_tmem = Geo::MAX_WARPS_TMEM / (Geo::T / 32);
+    slots = slots < by_tmem ? slots : by_tmem;
+    if (Geo::T > 32 && slots > 15) slots = 15;   // named barriers 1..15
+    *max_slots_out = slots;
+}
+
+int PCBP_CAT(bp3_occupancy_, PCBP_LOGN)(const LaunchGeom& g, int fkind)
+{
+    return fkind ? occupancy<1>(g) : occupancy<0>(g);
+}
+
+cudaError_t PCBP_CAT(bp3_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st)
+{
+    return fkind ? launch_variant<1>(P, g, st) : launch_variant<0>(P, g, st);
+}
+
+}  // namespace pcbp

@@ -1,6 +1,8 @@
 // Per-length launch entry points of the decoder kernels (one set per n):
 // bp_* from bp_inst.cu (per-stage kernel, used for the trace entry), bp2_*
-// from bp_inst2.cu (stage-grouped kernel, used by bp_decode).
+// from bp_inst2.cu (stage-grouped kernel, bp_decode for n < 8), bp3_* from
+// bp_inst3.cu (stage-grouped kernel with TMEM-resident group interiors,
+// bp_decode for n = 8..11).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -34,5 +36,17 @@ PCBP_DECLARE_LEN(10)
 PCBP_DECLARE_LEN(11)
 
 #undef PCBP_DECLARE_LEN
+
+#define PCBP_DECLARE_LEN3(n)                                                                  \
+    void bp3_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out); \
+    int bp3_occupancy_##n(const LaunchGeom& g, int fkind);                                     \
+    cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st);
+
+PCBP_DECLARE_LEN3(8)
+PCBP_DECLARE_LEN3(9)
+PCBP_DECLARE_LEN3(10)
+PCBP_DECLARE_LEN3(11)
+
+#undef PCBP_DECLARE_LEN3
 
 }  // namespace pcbp

@@ -274,3 +274,35 @@ def test_full_size_workload_sampled(pcbp, oracle):
     want = torch.from_numpy(pay).to(dev)[idx]
     fer = (got != want).any(dim=1).float().mean().item()
     assert fer < 0.05
+
+
+# --------------------------------------------------------------------------- the two production kernels
+KERNEL_CASES = [
+    (256, 128, 8, POLY8, 2.0, dict(mode=1, rho_range_fixed=4, P_level=7, N_min=3, T0=3), 60, 3000),
+    (512, 256, 24, POLY24, 1.75, dict(mode=1, P_range=9, P_level=8, D=40, N_min=2, T0=2, stop_kind=3), 80, 1500),
+    (1024, 512, 24, POLY24, 2.0, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=4, T0=4), 120, 2000),
+    (1024, 512, 24, POLY24, 1.5, dict(mode=1, P_range=2, P_level=1, N_min=2, T0=2, stop_kind=2), 40, 600),
+    (1024, 512, 24, POLY24, 1.75, dict(mode=2, it_reset_full=7, q_max=12), 90, 800),
+    (1024, 512, 24, POLY24, 2.0, dict(mode=1, rho_range_fixed=3, P_level=9, N_min=3, T0=3, fkind=1), 60, 800),
+    (2048, 1024, 24, POLY24, 2.0, dict(mode=1, P_range=11, P_level=10, N_min=2, T0=2, stop_kind=3), 40, 300),
+]
+
+
+@pytest.mark.parametrize("case", KERNEL_CASES, ids=lambda c: f"N{c[0]}-mode{c[5]['mode']}-f{c[5].get('fkind', 0)}")
+def test_tmem_and_grouped_kernels_agree(pcbp, oracle, monkeypatch, case):
+    """From N = 256 on, bp_decode keeps the interior messages of each stage
+    group in tensor memory; PCBP_DECODER=grouped selects the shared-memory
+    kernel.  Same arithmetic, so identical outputs, box-plus included (whose
+    transcendental functions the CPU oracle does not reproduce bit for bit)."""
+    N, K, r, poly, ebn0, kw, max_iters, B = case
+    _, _, _, llr = frames(oracle, N, K, r, poly, B, ebn0, seed=N * 13 + kw["mode"] + kw.get("fkind", 0))
+    s = pcbp.sched(**{"seed": 777, "stop_kind": 1, **kw})
+    code = pcbp.pc_construct(N, K, r, poly)
+    monkeypatch.delenv("PCBP_DECODER", raising=False)
+    bits, iters, ok, _ = gpu_decode(pcbp, code, llr, s, max_iters)
+    monkeypatch.setenv("PCBP_DECODER", "grouped")
+    gbits, giters, gok, _ = gpu_decode(pcbp, code, llr, s, max_iters)
+    assert np.array_equal(iters, giters)
+    assert np.array_equal(ok, gok)
+    assert np.array_equal(bits, gbits)
+    assert (iters > 2 * kw.get("T0", kw.get("it_reset_full", 1))).any()   # frames that went through switches
