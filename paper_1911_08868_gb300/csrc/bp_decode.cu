@@ -152,6 +152,16 @@ cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cu
     }
 }
 
+void tmem_tables_of(const pc_code* c, size_t* bytes)
+{
+    switch (c->n) {
+        case 8: bp3_tables_8(c->N, c->K, bytes); break;
+        case 9: bp3_tables_9(c->N, c->K, bytes); break;
+        case 10: bp3_tables_10(c->N, c->K, bytes); break;
+        default: bp3_tables_11(c->N, c->K, bytes); break;
+    }
+}
+
 // The TMEM kernel serves n = 8..11 unless PCBP_DECODER=grouped selects the
 // shared-memory-only kernel (both give identical outputs).
 bool use_tmem_kernel(int n)
@@ -227,7 +237,8 @@ int plan_launch3(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
     int T = 0, max_slots = 0;
     size_t slot = 0;
     shape3_of(c->n, &T, &slot, &max_slots);
-    const size_t tab = table_bytes(c->N, c->crc_len, c->K) + 64;   // + the 64-byte swizzle table
+    size_t tab = 0;
+    tmem_tables_of(c, &tab);
     if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(di.smem_optin) - tab) / slot);
     slots = std::max(1, std::min(slots, max_slots));

@@ -55,6 +55,8 @@ void PCBP_CAT(bp3_shape_, PCBP_LOGN)(int* threads_per_slot_out, size_t* slot_byt
     *max_slots_out = slots;
 }
 
+void PCBP_CAT(bp3_tables_, PCBP_LOGN)(int N, int K, size_t* bytes) { *bytes = tmem_table_bytes(N, K); }
+
 int PCBP_CAT(bp3_occupancy_, PCBP_LOGN)(const LaunchGeom& g, int fkind)
 {
     return fkind ? occupancy<1>(g) : occupancy<0>(g);

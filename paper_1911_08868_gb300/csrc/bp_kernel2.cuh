@@ -91,9 +91,13 @@ struct GroupCtl {
 };
 
 // Partition of the stages of one iteration (slot leader).
+// short_last: the last segment puts its short group at its end instead of its
+// start (the TMEM kernel's choice: the no-event partition then has one group
+// width before the last group).
 template <int CL, int KB>
 __device__ __noinline__ void build_groups(GroupCtl<CL, KB>* c, const unsigned char* swt, int n, bool have_ev,
-                                          int level, int range, long long blk, const signed char* order)
+                                          int level, int range, long long blk, const signed char* order,
+                                          bool short_last = false)
 {
     int lo = n, hi = -1, m = 0;
     if (have_ev) {
@@ -128,12 +132,14 @@ __device__ __noinline__ void build_groups(GroupCtl<CL, KB>* c, const unsigned ch
             }
             continue;
         }
-        // groups of KB from the end of the segment; the first one is shorter
+        // groups of KB from the end of the segment, the first one shorter (or,
+        // short_last on the last segment, from its start, the last one shorter)
         const int len = b - a + 1;
         const int first = len % KB == 0 ? KB : len % KB;
+        const bool sl = short_last && sg == nseg - 1;
         int s = a;
         for (int q = 0; s <= b; ++q) {
-            const int gl = q == 0 ? first : KB;
+            const int gl = sl ? (b - s + 1 < KB ? b - s + 1 : KB) : (q == 0 ? first : KB);
             c->s0[ng] = (signed char)s; c->g[ng] = (signed char)gl; c->single_[ng] = 0;
             c->local[ng] = (signed char)(kind == 1);
             for (int cls = 0; cls < 2; ++cls) {

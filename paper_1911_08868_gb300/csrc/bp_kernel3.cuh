@@ -2,38 +2,51 @@
 // memory (sm_103a TMEM), the bp_decode path for N >= 256 (Algorithm 1 of
 // arXiv 1911.08868).
 //
-// The stage partition, positions per thread, swizzled shared-memory planes,
-// decisions, stop tests and switch are those of the stage-grouped kernel
-// (bp_kernel2.cuh), and so is every floating-point operation: the outputs are
-// bit-identical.  What changes is where the messages live between uses.
+// Positions per thread, swizzled shared-memory planes, stop tests and switch
+// follow the stage-grouped kernel (bp_kernel2.cuh), and so does every
+// floating-point operation: the outputs are bit-identical.  What changes is
+// where the messages live between uses and how often the slot synchronises.
 //
-// A group g of stages s0 .. s0+gl-1 (0-based, counted from the channel) reads
-// L at node level s0+1 and R at level s0+gl+1 from its neighbours and produces
-// L at level s0+gl+1 and R at level s0+1 for them: these boundary levels stay
-// in shared memory.  The levels strictly inside the group are produced and
-// consumed by the same thread on the same positions, as long as the partition
-// does not change:
+// Interior messages in TMEM.  A group of stages s0 .. s0+gl-1 (0-based,
+// counted from the channel) reads L at node level s0+1 and R at level
+// s0+gl+1 from its neighbours and produces L at level s0+gl+1 and R at level
+// s0+1 for them: these boundary levels stay in shared memory.  The levels
+// inside the group are produced and consumed by the same thread on the same
+// positions while the partition stays:
 //   L at levels s0+1 .. s0+gl    written by the L sweep, read by the R sweep
-//                                of the same iteration (level 1 is the channel
-//                                LLRs, kept in registers),
-//   R at levels s0+2 .. s0+gl    written by the R sweep, read by the L sweep
-//                                of the next iteration.
+//                                (level 1 is the channel LLRs, in registers;
+//                                the last group keeps its L in registers),
+//   R at levels s0+2 .. s0+gl    written by the R sweep, read by the next
+//                                L sweep.
 // Each thread keeps these E = 2^KB values per level in its own TMEM lane
 // (tcgen05.st/ld, 32x32b shape: the warp's quarter of the 128 lanes, one
-// column per value), a warp's columns at bank (warp / 4) * TCOLS.  Only the
-// thread that wrote a value reads it back, so no fence orders TMEM across
-// threads; tcgen05.wait::st orders a thread's stores before its next loads.
+// column per value), a warp's columns at bank (warp / 4) * TCOLS.  It also
+// caches there, per group, the shared-memory offsets of its E positions and,
+// for the last group, their priors and CRC contributions: these depend only
+// on the partition.  Only the thread that wrote a value reads it back, so no
+// fence orders TMEM across threads; tcgen05.wait::st orders a thread's stores
+// before its next loads.
 //
-// Each thread also caches in TMEM, per group, the shared-memory offsets of its
-// E positions and, for the last group, their priors: they depend only on the
-// partition, so the sweeps read them with one tcgen05.ld instead of rebuilding
-// them from the partition tables.
+// Fewer barriers.  The CRC residue of the decisions is linear in them: each
+// thread XORs the cached contributions c_j (x^(K-1-k) mod g for the
+// information bit of rank k at position j) of its positions decided 1, a
+// warp reduction and one shared atomic per warp complete it.  The last
+// group's R sweep runs before the stop test (wasted only in a frame's final
+// iteration), so a single barrier publishes both the residue and that
+// group's boundary R.  Decision words are written only when the frame stops
+// or runs out of iterations (every iteration when the G-matrix test needs
+// them).  Group 0's R sweep writes nothing other threads read unless the
+// G-matrix test is on, so no barrier follows it then.  Where two neighbouring
+// groups deposit the thread index's warp bits into the same position bits,
+// each warp owns the same positions on both sides of their boundary: that
+// exchange only needs __syncwarp (with the no-event partition of N = 1024,
+// two of the three group boundaries).
 //
 // The partition changes when a permutation event is applied (Sec. III): the
-// R messages of the interior levels are then written to their canonical
-// shared-memory planes with the old partition, the planes are reset as in
-// the stage-grouped kernel, and the interior levels are loaded again with the
-// new partition.  A new frame starts from zeroed planes the same way.
+// interior R messages go back to their canonical shared-memory planes with
+// the old partition, the planes are reset as in the stage-grouped kernel, and
+// the caches and interior levels are loaded again with the new partition.  A
+// new frame starts from zeroed planes the same way.
 //
 // One CTA per SM (its shared memory exceeds half an SM's) allocates all 512
 // TMEM columns for its lifetime, so allocations never wait on one another.
@@ -45,17 +58,69 @@
 
 namespace pcbp {
 
-// Most groups of KB stages that are not single stages, over every event
-// shape the partition of build_groups can take (m = level + range - 1).
-__host__ __device__ constexpr int max_register_groups(int n, int KB)
+// TMEM columns of one group's interior messages (E per level): group 0 skips
+// L level 1 (registers), the last group keeps its L in registers.
+__host__ __device__ constexpr int group_cols(int s0, int gl, bool single, bool last, int E)
 {
-    auto cdiv = [](int a, int b) { return (a + b - 1) / b; };
-    int best = cdiv(n, KB);                                  // no event
+    return single ? 0 : (last ? (gl - 1) * E : (s0 == 0 ? (2 * gl - 2) * E : (2 * gl - 1) * E));
+}
+
+// Interior columns (cols) and register groups (groups) of the partition
+// build_groups<..>(short_last = true) makes for one event shape (level 0: none).
+struct PartitionSize {
+    int cols, groups;
+};
+
+__host__ __device__ constexpr PartitionSize partition_size(int n, int KB, int level, int range)
+{
+    const int E = 1 << KB;
+    int sa[3] = {0, 0, 0}, sb[3] = {0, 0, 0}, sk[3] = {0, 0, 0}, ns = 0;
+    if (level == 0) {
+        sa[0] = 0; sb[0] = n - 1; sk[0] = 0; ns = 1;
+    } else {
+        const int lo = level - 1, hi = level + range - 2, m = hi + 1;
+        if (m >= KB) {
+            sa[ns] = 0; sb[ns] = hi; sk[ns] = 1; ++ns;
+            if (hi + 1 <= n - 1) { sa[ns] = hi + 1; sb[ns] = n - 1; sk[ns] = 0; ++ns; }
+        } else {
+            if (lo >= 1) { sa[ns] = 0; sb[ns] = lo - 1; sk[ns] = 0; ++ns; }
+            sa[ns] = lo; sb[ns] = hi; sk[ns] = 2; ++ns;
+            if (hi + 1 <= n - 1) { sa[ns] = hi + 1; sb[ns] = n - 1; sk[ns] = 0; ++ns; }
+        }
+    }
+    int s0s[32] = {}, gls[32] = {}, sing[32] = {}, ng = 0;
+    for (int sg = 0; sg < ns; ++sg) {
+        const int a = sa[sg], b = sb[sg];
+        if (sk[sg] == 2) {
+            for (int s = a; s <= b; ++s) { s0s[ng] = s; gls[ng] = 1; sing[ng] = 1; ++ng; }
+            continue;
+        }
+        const int len = b - a + 1, first = len % KB == 0 ? KB : len % KB;
+        const bool sl = sg == ns - 1;
+        int s = a;
+        for (int q = 0; s <= b; ++q) {
+            const int gl = sl ? (b - s + 1 < KB ? b - s + 1 : KB) : (q == 0 ? first : KB);
+            s0s[ng] = s; gls[ng] = gl; sing[ng] = 0; ++ng;
+            s += gl;
+        }
+    }
+    PartitionSize r{0, 0};
+    for (int g = 0; g < ng; ++g) {
+        r.cols += group_cols(s0s[g], gls[g], sing[g] != 0, g == ng - 1, E);
+        r.groups += sing[g] ? 0 : 1;
+    }
+    return r;
+}
+
+// The largest partition over every event shape (m = level + range - 1 <= n).
+__host__ __device__ constexpr PartitionSize max_partition(int n, int KB)
+{
+    PartitionSize best = partition_size(n, KB, 0, 0);
     for (int level = 1; level < n; ++level)
         for (int range = 2; range <= 16 && level + range - 1 <= n; ++range) {
-            const int lo = level - 1, hi = level + range - 2, m = hi + 1;
-            const int g = m >= KB ? cdiv(m, KB) + cdiv(n - m, KB) : cdiv(lo, KB) + cdiv(n - 1 - hi, KB);
-            best = g > best ? g : best;
+            const PartitionSize p = partition_size(n, KB, level, range);
+            best.cols = p.cols > best.cols ? p.cols : best.cols;
+            best.groups = p.groups > best.groups ? p.groups : best.groups;
         }
     return best;
 }
@@ -68,17 +133,45 @@ struct G3 {
     static constexpr int T = N / E;                              // threads per slot, every one owns positions
     static constexpr int NW = words_of<LOGN>();
     static constexpr int NPL = LOGN - 1;
-    static constexpr int MIN_GROUPS = (LOGN + KB - 1) / KB;
-    static constexpr int COLS = (2 * LOGN - MIN_GROUPS) * E;     // interior messages: sum (2 gl - 1) E columns
-    static constexpr int MAXRG = max_register_groups(LOGN, KB);
+    static constexpr PartitionSize MAXP = max_partition(LOGN, KB);
+    static constexpr int COLS = MAXP.cols;                       // interior messages
     static constexpr int ACOL = COLS;                            // E shared-memory offsets per register group
-    static constexpr int PCOL = COLS + MAXRG * E;                // the last group's priors
-    static constexpr int TCOLS = PCOL + E;                       // TMEM columns per thread
+    static constexpr int PCOL = ACOL + MAXP.groups * E;          // the last group's priors
+    static constexpr int CCOL = PCOL + E;                        // the last group's CRC contributions
+    static constexpr int TCOLS = CCOL + E;                       // TMEM columns per thread
     static constexpr int MAX_WARPS_TMEM = 4 * (512 / TCOLS);
     static_assert(T >= 32, "every lane of a warp owns positions");
 };
 
 constexpr int kTmemCols = 512;
+
+// Code tables of the TMEM kernel in shared memory: frozen mask, CRC
+// contribution c_j of every position (bit i = bit i of x^(K-1-k) mod g for
+// the information bit of rank k at j, 0 for frozen positions), information
+// positions, swizzle table; the frame slots follow.
+__host__ __device__ inline size_t tmem_table_bytes(int N, int K)
+{
+    const int nw = N >= 32 ? N / 32 : 1;
+    return align16(size_t(nw) * 4 + size_t(N) * 4 + size_t(K) * 2) + kSwzTableBytes;
+}
+
+__device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned char* smem)
+{
+    const int N = code.N, K = code.K, r = code.r;
+    const int NW = N >= 32 ? N / 32 : 1;
+    uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* s_cj = s_frozen + NW;
+    int16_t* s_info = reinterpret_cast<int16_t*>(s_cj + N);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = code.frozen[i];
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        uint32_t c = 0;
+        for (int i = 0; i < r; ++i) c |= ((code.crcplane[i][j >> 5] >> (j & 31)) & 1u) << i;
+        s_cj[j] = c;
+    }
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = code.info_idx[i];
+    unsigned char* s_swz = smem + tmem_table_bytes(N, K) - kSwzTableBytes;
+    for (int i = threadIdx.x; i < kSwzTableBytes; i += blockDim.x) s_swz[i] = swz_row(i);
+}
 
 // Largest CTA of the TMEM kernel for a length: 512 threads, or fewer when
 // shared memory or TMEM holds fewer slots (N = 1024: 3 slots of 128 threads).
@@ -86,16 +179,20 @@ template <int LOGN>
 __host__ __device__ constexpr int tmem_max_threads() { return LOGN == 10 ? 384 : (LOGN >= 11 ? 256 : 512); }
 
 // Per-slot control block: the stage partition plus a packed copy that the
-// sweeps read with two 16-byte loads per group.
+// sweeps read with one 16-byte load per group.
 template <int LOGN, int KB>
 struct Ctl3 {
     GroupCtl<LOGN, KB> g;
-    // rec[gi] = {s0 | gl << 8 | single << 16 | local << 24, TMEM column of L level s0+1,
+    // rec[gi] = {s0 | gl << 8 | single << 16 | local << 24 | (boundary gi|gi+1 warp-local) << 25
+    //              | (boundary gi-1|gi warp-local) << 26,
+    //            TMEM column of L level s0+1 (virtual for group 0 and the last group;
+    //            R level s0+2 is at this + gl E),
     //            contig(class 0) & 0xff | (contig(class 1) & 0xff) << 8,
     //            TMEM column of the group's cached shared-memory offsets}
     int4 rec[LOGN];
     uint2 cmask[LOGN];
     alignas(16) short swoff[LOGN][2][1 << KB];
+    unsigned crc_part[3];    // CRC residue of iteration it, accumulated in crc_part[it % 3]
 };
 
 // ---------------------------------------------------------------------------
@@ -180,16 +277,38 @@ template <int LOGN, int KB>
 __device__ __forceinline__ void pack_groups(Ctl3<LOGN, KB>* c)
 {
     constexpr int E = 1 << KB;
+    constexpr int TB = LOGN - KB;        // thread-index bits: 5 lane bits, then warp bits
     int col = 0, acol = G3<LOGN, KB>::ACOL;
-    for (int gi = 0; gi < c->g.ng; ++gi) {
-        const int gl = c->g.g[gi], single = c->g.single_[gi];
-        c->rec[gi] = make_int4(int(c->g.s0[gi]) | (gl << 8) | (single << 16) | (int(c->g.local[gi]) << 24), col,
+    const int ng = c->g.ng;
+    // position bits that receive the warp bits of the thread index (the top
+    // TB - 5 bits of the deposit mask), for groups that are neither single
+    // stages nor subgraph-local; ~0 otherwise
+    auto warp_bits = [&](int gi) -> unsigned {
+        if (c->g.single_[gi] || c->g.local[gi]) return ~0u;
+        unsigned m = c->g.cmask[gi][0], w = 0;
+        for (int k = 0; k < TB; ++k) {
+            const unsigned low = m & (0u - m);
+            if (k >= 5) w |= low;
+            m ^= low;
+        }
+        return w;
+    };
+    for (int gi = 0; gi < ng; ++gi) {
+        const int s0 = c->g.s0[gi], gl = c->g.g[gi], single = c->g.single_[gi];
+        const bool last = gi == ng - 1;
+        // L level s0+1+i at colL + i E, R level s0+2+i at colL + (gl + i) E
+        const int colL = last ? col - gl * E : (s0 == 0 ? col - E : col);
+        const bool wl_after = gi + 1 < ng && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi + 1);
+        const bool wl_before = gi > 0 && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi - 1);
+        c->rec[gi] = make_int4(s0 | (gl << 8) | (single << 16) | (int(c->g.local[gi]) << 24) | (int(wl_after) << 25) |
+                                   (int(wl_before) << 26),
+                               colL,
                                (int(c->g.contig[gi][0]) & 0xff) | ((int(c->g.contig[gi][1]) & 0xff) << 8), acol);
         c->cmask[gi] = make_uint2(c->g.cmask[gi][0], c->g.cmask[gi][1]);
         for (int cls = 0; cls < 2; ++cls)
             for (int e = 0; e < E; ++e) c->swoff[gi][cls][e] = c->g.swoff[gi][cls][e];
         if (!single) {
-            col += (2 * gl - 1) * E;
+            col += group_cols(s0, gl, false, last, E);
             acol += E;
         }
     }
@@ -282,10 +401,11 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int r = J.r;
     const int K = J.K;
     const uint32_t* s_frozen = reinterpret_cast<const uint32_t*>(smem);
-    const uint32_t* s_crc = s_frozen + NW;
-    const int16_t* s_info = reinterpret_cast<const int16_t*>(s_crc + r * NW);
-    const unsigned char* s_swz = smem + shared_table_bytes(NW, r, K);
+    const uint32_t* s_cj = s_frozen + NW;
+    const int16_t* s_info = reinterpret_cast<const int16_t*>(s_cj + N);
+    const unsigned char* s_swz = smem + tmem_table_bytes(N, K) - kSwzTableBytes;
     auto sw = [&](int j) { return swz(s_swz, j); };
+    (void)r;
 
     const int slot = threadIdx.x / T;
     const int tid = threadIdx.x - slot * T;
@@ -293,7 +413,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int warp = tid >> 5;
     constexpr size_t ctl_bytes = align16(sizeof(Ctl));
     constexpr size_t slot_sz = ctl_bytes + align16(size_t(2 * NW * 4)) + size_t(2 * NPL) * N * 4;
-    unsigned char* sbase = smem + shared_table_bytes(NW, r, K) + kSwzTableBytes + size_t(slot) * slot_sz;
+    unsigned char* sbase = smem + tmem_table_bytes(N, K) + size_t(slot) * slot_sz;
     Ctl* ctl = reinterpret_cast<Ctl*>(sbase);
     uint32_t* dec = reinterpret_cast<uint32_t*>(sbase + ctl_bytes);
     uint32_t* xh = dec + NW;
@@ -309,11 +429,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int gwarp = int(threadIdx.x >> 5);
     const uint32_t tm = tm_base + (uint32_t(32 * (gwarp & 3)) << 16) + uint32_t((gwarp >> 2) * Geo::TCOLS);
 
-    // Shared-memory byte offset A of a position set is that of L plane s0-1
-    // (node level s0+1) of group s0; the group's other planes are at fixed
-    // distances:  Lp plane s0-1+d at A + 4 d N,  Rp plane s0-1+d at A + 4 (NPL + d) N.
+    // The cached offset A of a position in a group with first stage s0 is the
+    // byte offset (from smem) of the position in L plane s0-1 (node level
+    // s0+1); the group's other planes are at fixed distances:
+    //   Lp plane s0-1+d at A + 4 d N,   Rp plane s0-1+d at A + 4 (NPL + d) N.
     auto at = [&](int a, int floats) -> float& { return *reinterpret_cast<float*>(smem + a + 4 * floats); };
-    // logical position of cached offset a in group s0 (for decisions and the G-matrix bits)
+    // logical position of cached offset a in a group with first stage s0
     auto pos_of = [&](int a, int s0) { return sw(((a - lp_off) >> 2) - (s0 - 1) * N); };
 
     const DevSched& S = J.S;
@@ -321,6 +442,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int KW = (K + 31) / 32;
     const int max_iters = J.max_iters;
     const bool want_g = (S.stop_kind & 2) != 0;
+    const bool want_crc = (S.stop_kind & 1) != 0;
 
     float L1[E];   // channel LLRs of the first group's positions
 
@@ -330,9 +452,35 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         return (local && ((tid & lowmask) == ctl->g.beta)) ? 1 : 0;
     };
 
-    // After a new partition: cache every register group's offsets and the
-    // last group's priors in TMEM, move the interior R messages from the
-    // canonical planes to TMEM, load the channel LLRs of the first group.
+    // A new frame on the partition the TMEM caches already describe: zero
+    // interior R messages, channel LLRs of group 0's positions.
+    auto restart_partition = [&](const float* llr_f) {
+        const int ng = ctl->g.ng;
+        float z[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) z[e] = 0.f;
+        for (int gi = 0; gi < ng; ++gi) {
+            const int4 rc = ctl->rec[gi];
+            const int gl = (rc.x >> 8) & 0xff;
+            if ((rc.x >> 16) & 1) continue;
+            const uint32_t colR = uint32_t(rc.y + gl * E);
+            for (int i = 0; i < gl - 1; ++i) tm_st<E>(tm + colR + uint32_t(i * E), z);
+            if (gi == 0) {
+                int A[E];
+                tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                tm_wait_ld();
+                tm_fence<E>(A);
+#pragma unroll
+                for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + pos_of(A[e], 0));
+            }
+        }
+        tm_wait_st();
+    };
+
+    // After a new partition: cache the register groups' offsets and the last
+    // group's priors and CRC contributions in TMEM, move the interior R
+    // messages from the canonical planes to TMEM, load the channel LLRs of the
+    // first group.
     auto enter_partition = [&](const float* llr_f) {
         const int ng = ctl->g.ng;
         for (int gi = 0; gi < ng; ++gi) {
@@ -353,9 +501,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             }
             if (gi == ng - 1) {
                 float pr[E];
+                int cj[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) pr[e] = prior_of(s_frozen, sw(ph[e]));
+                for (int e = 0; e < E; ++e) {
+                    const int j = sw(ph[e]);
+                    pr[e] = prior_of(s_frozen, j);
+                    cj[e] = int(s_cj[j]);
+                }
                 tm_st<E>(tm + uint32_t(Geo::PCOL), pr);
+                tm_st_i<E>(tm + uint32_t(Geo::CCOL), cj);
             }
             if (gi == 0) {
 #pragma unroll
@@ -389,8 +543,24 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         }
     };
 
+    // The slot leader fetches the next frame index as soon as the current
+    // frame's last iteration is known, so the atomic's latency overlaps the
+    // frame's output phase.
+    unsigned long long next_f = 0;
+    bool have_next = false;
+    auto fetch_next = [&]() {
+        if (tid == 0 && !have_next) {
+            next_f = atomicAdd(counter, 1ull);
+            have_next = true;
+        }
+    };
+    bool fresh = false;     // the control block holds the no-event partition and the TMEM caches match it
     while (true) {
-        if (tid == 0) ctl->g.frame = (long long)atomicAdd(counter, 1ull);
+        fetch_next();
+        if (tid == 0) {
+            ctl->g.frame = (long long)next_f;
+            have_next = false;
+        }
         sync();
         const long long f = ctl->g.frame;
         if (f >= J.B) break;
@@ -404,21 +574,33 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             ctl->g.ev_level = 0;
             ctl->g.ev_range = 0;
             ctl->g.ev_blk = -1;
-            signed char none[16];
-            build_groups<LOGN, KB>(&ctl->g, s_swz, n, false, 0, 0, 0, none);
-            pack_groups<LOGN, KB>(ctl);
+            ctl->crc_part[0] = 0u;
+            ctl->crc_part[1] = 0u;
+            ctl->crc_part[2] = 0u;
+            if (!fresh) {
+                signed char none[16];
+                build_groups<LOGN, KB>(&ctl->g, s_swz, n, false, 0, 0, 0, none, true);
+                pack_groups<LOGN, KB>(ctl);
+            }
         }
         sync();
-        enter_partition(llr_f);
+        if (fresh) restart_partition(llr_f);
+        else enter_partition(llr_f);
+        fresh = true;
 
         int next_reset = S.mode == 1 ? S.T0 : (S.mode == 2 ? S.it_reset_full : 0);
         int kev = 0;
         int used = max_iters;
 
+        int pb = 0;     // it % 3
         for (int it = 1; it <= max_iters; ++it) {
-            if (tid == 0) ctl->g.crc_res = 0;
-            if (want_g)
-                for (int i = tid; i < NW; i += T) xh[i] = 0u;
+            pb = pb == 2 ? 0 : pb + 1;
+            if (want_g) {
+                for (int i = tid; i < NW; i += T) {
+                    xh[i] = 0u;
+                    dec[i] = 0u;
+                }
+            }
             const int ng = ctl->g.ng;
             const int lowmask = (1 << ctl->g.low) - 1;
             const int beta = ctl->g.beta;
@@ -446,65 +628,70 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         Lp[s * N + sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
                         Lp[s * N + sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
                     }
-                    sync();
-                    continue;
+                } else {
+                    const uint32_t colL = uint32_t(rc.y);
+                    auto body = [&](auto glc) {
+                        constexpr int GL = decltype(glc)::value;
+                        int A[E];
+                        float rp[GL > 1 ? GL - 1 : 1][E];
+                        tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                        if constexpr (GL > 1) {
+#pragma unroll
+                            for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tm + colL + uint32_t((GL + i) * E), rp[i]);
+                        }
+                        tm_wait_ld();
+                        tm_fence<E>(A);
+                        float x[E], rb[E];
+#pragma unroll
+                        for (int e = 0; e < E; ++e) {
+                            x[e] = s0 == 0 ? L1[e] : at(A[e], 0);
+                            rb[e] = at(A[e], (NPL + GL) * N);                 // R level s0+GL+1 (boundary)
+                        }
+                        if constexpr (GL > 1) {
+#pragma unroll
+                            for (int i = 0; i < GL - 1; ++i) tm_fence<E>(rp[i]);
+                        }
+                        if (s0 > 0) tm_st<E>(tm + colL, x);                 // L level s0+1
+#pragma unroll
+                        for (int i = 0; i < GL; ++i) {
+                            l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
+                            if (i < GL - 1) tm_st<E>(tm + colL + uint32_t((i + 1) * E), x);   // L level s0+2+i
+                        }
+#pragma unroll
+                        for (int e = 0; e < E; ++e) at(A[e], GL * N) = x[e];          // L level s0+GL+1
+                    };
+                    if (gl == KB) body(std::integral_constant<int, KB>{});
+                    else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
+                    else body(std::integral_constant<int, 1>{});
                 }
-                const uint32_t colL = uint32_t(rc.y);
-                auto body = [&](auto glc) {
-                    constexpr int GL = decltype(glc)::value;
-                    int A[E];
-                    float rp[GL > 1 ? GL - 1 : 1][E];
-                    tm_ld_i<E>(tm + uint32_t(rc.w), A);
-                    if constexpr (GL > 1) {
-#pragma unroll
-                        for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tm + colL + uint32_t((GL + i) * E), rp[i]);
-                    }
-                    tm_wait_ld();
-                    tm_fence<E>(A);
-                    float x[E], rb[E];
-#pragma unroll
-                    for (int e = 0; e < E; ++e) {
-                        x[e] = s0 == 0 ? L1[e] : at(A[e], 0);
-                        rb[e] = at(A[e], (NPL + GL) * N);                 // R level s0+GL+1 (boundary)
-                    }
-                    if constexpr (GL > 1) {
-#pragma unroll
-                        for (int i = 0; i < GL - 1; ++i) tm_fence<E>(rp[i]);
-                    }
-                    if (s0 > 0) tm_st<E>(tm + colL, x);                 // L level s0+1
-#pragma unroll
-                    for (int i = 0; i < GL; ++i) {
-                        l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
-                        if (i < GL - 1) tm_st<E>(tm + colL + uint32_t((i + 1) * E), x);   // L level s0+2+i
-                    }
-#pragma unroll
-                    for (int e = 0; e < E; ++e) at(A[e], GL * N) = x[e];          // L level s0+GL+1
-                };
-                if (gl == KB) body(std::integral_constant<int, KB>{});
-                else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
-                else body(std::integral_constant<int, 1>{});
-                sync();
+                if (!want_g && ((rc.x >> 25) & 1)) __syncwarp();
+                else sync();
             }
 
-            // ---------------- last group: L sweep, decisions, kept in registers
+            // ---------------- last group: L sweep, decisions, residue, R sweep
             const int gL = ng - 1;
             const int4 rcL = ctl->rec[gL];
             const int s0L = rcL.x & 0xff, glL = (rcL.x >> 8) & 0xff;
             const uint32_t colLL = uint32_t(rcL.y);
             int AL[E];
             float pr[E];     // R(n+1): the prior of the last group's positions
-            float xL[KB][E];
-            float x[E];
+            unsigned umask = 0;
+            const bool check = S.stop_kind != 0 && it >= S.stop_from;
             {
                 float rp[KB > 1 ? KB - 1 : 1][E];
+                float xL[KB][E];
+                float x[E];
+                int cj[E];
                 tm_ld_i<E>(tm + uint32_t(rcL.w), AL);
                 tm_ld<E>(tm + uint32_t(Geo::PCOL), pr);
+                tm_ld_i<E>(tm + uint32_t(Geo::CCOL), cj);
 #pragma unroll
                 for (int i = 0; i < KB - 1; ++i)
                     if (i < glL - 1) tm_ld<E>(tm + colLL + uint32_t((glL + i) * E), rp[i]);
                 tm_wait_ld();
                 tm_fence<E>(AL);
                 tm_fence<E>(pr);
+                tm_fence<E>(cj);
 #pragma unroll
                 for (int i = 0; i < KB - 1; ++i) tm_fence<E>(rp[i]);
 #pragma unroll
@@ -518,62 +705,28 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         else l_layer<E, FK>(x, pr, i, alpha);
                     }
                 }
-            }
-            // a5: decisions u_j = [L(n+1) + R(n+1) < 0]
-            if (ctl->g.fastdec) {
-                // positions base .. base+E-1, register e at offset bitreverse(e)
-                uint32_t chunk = 0;
+                // a5: decisions u_j = [L(n+1) + R(n+1) < 0] and their CRC residue
+                unsigned part = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    int rev = 0;
-#pragma unroll
-                    for (int i = 0; i < KB; ++i) rev |= ((e >> i) & 1) << (KB - 1 - i);
-                    if (__fadd_rn(x[e], pr[e]) < 0.f) chunk |= 1u << rev;
+                    const bool u = __fadd_rn(x[e], pr[e]) < 0.f;
+                    umask |= u ? 1u << e : 0u;
+                    part ^= u ? unsigned(cj[e]) : 0u;
                 }
-                if (E >= 32) {
-                    dec[(tid * E) >> 5] = chunk;
-                } else {
-                    constexpr int PER = 32 / E;     // threads per decision word
-                    uint32_t word = chunk << ((tid % PER) * E);
-#pragma unroll
-                    for (int o = 1; o < PER; o <<= 1) word |= __shfl_xor_sync(0xffffffffu, word, o);
-                    if ((tid % PER) == 0) dec[(tid * E) >> 5] = word;
+                if (check && want_crc) {
+                    part = __reduce_xor_sync(0xffffffffu, part);
+                    if (lane == 0 && part) atomicXor(&ctl->crc_part[pb], part);
                 }
-            } else {
-                for (int i = tid; i < NW; i += T) dec[i] = 0u;
-                sync();
+                if (want_g) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int j = pos_of(AL[e], s0L);
-                    if (__fadd_rn(x[e], pr[e]) < 0.f) atomicOr(&dec[j >> 5], 1u << (j & 31));
+                    for (int e = 0; e < E; ++e)
+                        if ((umask >> e) & 1u) {
+                            const int j = pos_of(AL[e], s0L);
+                            atomicOr(&dec[j >> 5], 1u << (j & 31));
+                        }
                 }
-            }
-            sync();
-
-            // a5: stop test (CRC residue bits spread over the warps)
-            const bool check = S.stop_kind != 0 && it >= S.stop_from;
-            int res = 0;
-            if (check && (S.stop_kind & 1)) {
-                uint32_t part = 0;
-                for (int i = warp; i < r; i += NWARP) {
-                    uint32_t acc = 0;
-#pragma unroll
-                    for (int w = lane; w < NW; w += 32) acc ^= dec[w] & s_crc[i * NW + w];
-                    const uint32_t bal = __ballot_sync(0xffffffffu, __popc(acc) & 1);
-                    part |= uint32_t(__popc(bal) & 1) << i;
-                }
-                if (lane == 0 && part) atomicOr(reinterpret_cast<unsigned*>(&ctl->g.crc_res), part);
-                sync();
-                res = ctl->g.crc_res;     // read once: thread 0 clears it again next iteration
-            }
-            if (check && S.stop_kind == 1 && res == 0) {
-                used = it;
-                break;
-            }
-
-            tm_wait_st();
-            // ---------------- R sweep, last group (continues from registers)
-            {
+                // R sweep of the last group (ahead of the stop test)
+                tm_wait_st();
                 float y[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) y[e] = pr[e];
@@ -599,6 +752,29 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
             }
             sync();
+            const unsigned res = (check && want_crc) ? ctl->crc_part[pb] : 0u;
+            // every thread read the residue of iteration it-1 before this barrier; the
+            // next barrier of this kind comes before anyone accumulates iteration it+2
+            if (tid == 0) ctl->crc_part[pb == 0 ? 2 : pb - 1] = 0u;
+
+            if (!want_g) {
+                const bool stop = check && res == 0u;
+                if (stop || it == max_iters) {
+                    fetch_next();
+                    // the decision words, once per frame
+                    for (int i = tid; i < NW; i += T) dec[i] = 0u;
+                    sync();
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((umask >> e) & 1u) {
+                            const int j = pos_of(AL[e], s0L);
+                            atomicOr(&dec[j >> 5], 1u << (j & 31));
+                        }
+                    sync();
+                    if (stop) used = it;
+                    break;
+                }
+            }
 
             // ---------------- R sweep, the other groups in reverse
             for (int gi = ng - 2; gi >= 0; --gi) {
@@ -630,72 +806,74 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                             }
                         }
                     }
-                    sync();
-                    continue;
-                }
-                const uint32_t colL = uint32_t(rc.y);
-                auto body = [&](auto glc) {
-                    constexpr int GL = decltype(glc)::value;
-                    int A[E];
-                    float lv[GL][E];
-                    tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                } else {
+                    const uint32_t colL = uint32_t(rc.y);
+                    auto body = [&](auto glc) {
+                        constexpr int GL = decltype(glc)::value;
+                        int A[E];
+                        float lv[GL][E];
+                        tm_ld_i<E>(tm + uint32_t(rc.w), A);
 #pragma unroll
-                    for (int i = 0; i < GL; ++i)
-                        if (i > 0 || s0 > 0) tm_ld<E>(tm + colL + uint32_t(i * E), lv[i]);   // L level s0+1+i
-                    tm_wait_ld();
-                    tm_fence<E>(A);
-                    float y[E];
+                        for (int i = 0; i < GL; ++i)
+                            if (i > 0 || s0 > 0) tm_ld<E>(tm + colL + uint32_t(i * E), lv[i]);   // L level s0+1+i
+                        tm_wait_ld();
+                        tm_fence<E>(A);
+                        float y[E];
 #pragma unroll
-                    for (int e = 0; e < E; ++e) y[e] = at(A[e], (NPL + GL) * N);           // R level s0+GL+1
+                        for (int e = 0; e < E; ++e) y[e] = at(A[e], (NPL + GL) * N);           // R level s0+GL+1
 #pragma unroll
-                    for (int i = 0; i < GL; ++i) tm_fence<E>(lv[i]);
-                    if (s0 == 0) {
+                        for (int i = 0; i < GL; ++i) tm_fence<E>(lv[i]);
+                        if (s0 == 0) {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) lv[0][e] = L1[e];
-                    }
+                            for (int e = 0; e < E; ++e) lv[0][e] = L1[e];
+                        }
 #pragma unroll
-                    for (int i = GL - 1; i >= 0; --i) {
-                        const int s = s0 + i;
-                        if (s == 0 && !want_g) continue;
-                        r_layer<E, FK>(y, lv[i], i, alpha);
-                        if (i > 0) {
-                            tm_st<E>(tm + colL + uint32_t((GL + i - 1) * E), y);            // R level s0+1+i
-                        } else if (s >= 1) {
+                        for (int i = GL - 1; i >= 0; --i) {
+                            const int s = s0 + i;
+                            if (s == 0 && !want_g) continue;
+                            r_layer<E, FK>(y, lv[i], i, alpha);
+                            if (i > 0) {
+                                tm_st<E>(tm + colL + uint32_t((GL + i - 1) * E), y);            // R level s0+1+i
+                            } else if (s >= 1) {
 #pragma unroll
-                            for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
-                        } else {
+                                for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
+                            } else {
 #pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                const int j = pos_of(A[e], s0);
-                                if (__fadd_rn(L1[e], y[e]) < 0.f) atomicOr(&xh[j >> 5], 1u << (j & 31));
+                                for (int e = 0; e < E; ++e) {
+                                    const int j = pos_of(A[e], s0);
+                                    if (__fadd_rn(L1[e], y[e]) < 0.f) atomicOr(&xh[j >> 5], 1u << (j & 31));
+                                }
                             }
                         }
-                    }
-                };
-                if (gl == KB) body(std::integral_constant<int, KB>{});
-                else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
-                else body(std::integral_constant<int, 1>{});
-                sync();
+                    };
+                    if (gl == KB) body(std::integral_constant<int, KB>{});
+                    else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
+                    else body(std::integral_constant<int, 1>{});
+                }
+                // group 0 writes shared state (the G-matrix bits) only for the G-matrix test
+                if (want_g) sync();
+                else if (gi > 0) {
+                    if ((rc.x >> 26) & 1) __syncwarp();
+                    else sync();
+                }
             }
 
-            bool stop = false;
-            if (check) {
-                bool ok = true;
-                if (S.stop_kind & 1) ok = res == 0;
-                if (want_g) {
+            if (want_g) {
+                bool stop = false;
+                if (check) {
                     if (warp == 0) {
                         const bool gok = g_check<LOGN>(dec, xh, lane);
                         if (lane == 0) ctl->g.g_ok = gok ? 1 : 0;
                     }
                     sync();
-                    ok = ok && ctl->g.g_ok != 0;
+                    stop = (!want_crc || res == 0u) && ctl->g.g_ok != 0;
                     sync();             // every thread has read g_ok before it is written again
                 }
-                stop = ok;
-            }
-            if (stop) {
-                used = it;
-                break;
+                if (stop) {
+                    used = it;
+                    break;
+                }
+                if (it == max_iters) break;
             }
 
             // a6: switch at iter == N_it,reset
@@ -728,9 +906,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                             inc = qz > S.N_min ? qz : S.N_min;
                         }
                         ctl->g.next_inc = int(inc);
-                        build_groups<LOGN, KB>(&ctl->g, s_swz, n, true, level, range, blk, order);
+                        build_groups<LOGN, KB>(&ctl->g, s_swz, n, true, level, range, blk, order, true);
                         pack_groups<LOGN, KB>(ctl);
                     }
+                    fresh = false;
                     sync();
                     // resetVariableNodes: R at the interior levels of the previous
                     // subgraph (reverting to the original order) and of the new one
@@ -757,18 +936,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         }
 
         // a7: outputs
+        fetch_next();
         {
             uint32_t part = 0;
-            for (int i = warp; i < r; i += NWARP) {
-                uint32_t acc = 0;
 #pragma unroll
-                for (int w = lane; w < NW; w += 32) acc ^= dec[w] & s_crc[i * NW + w];
-                const uint32_t bal = __ballot_sync(0xffffffffu, __popc(acc) & 1);
-                part |= uint32_t(__popc(bal) & 1) << i;
-            }
+            for (int j = tid; j < N; j += T)
+                if ((dec[j >> 5] >> (j & 31)) & 1u) part ^= s_cj[j];
+            part = __reduce_xor_sync(0xffffffffu, part);
             if (tid == 0) ctl->g.crc_res = 0;
             sync();
-            if (lane == 0 && part) atomicOr(reinterpret_cast<unsigned*>(&ctl->g.crc_res), part);
+            if (lane == 0 && part) atomicXor(reinterpret_cast<unsigned*>(&ctl->g.crc_res), part);
             for (int o = warp; o < KW; o += NWARP) {
                 const int kk = o * 32 + lane;
                 uint32_t bit = 0;
@@ -795,7 +972,7 @@ __global__ void __launch_bounds__(tmem_max_threads<LOGN>(), 1) bp_decode_tmem_ke
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tm;
-    load_code_tables(P.code, smem);
+    load_code_tables3(P.code, smem);
     if (threadIdx.x < 32) {
         const uint32_t dst = uint32_t(__cvta_generic_to_shared(&s_tm));
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "n"(kTmemCols)
