@@ -189,13 +189,16 @@ int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w
                      const double* d_ckpt, const double* d_glogits, double* d_gw, double* d_gllr,
                      void* d_workspace, void* stream);
 
-/* ---- Mixed-length batched decoding (one persistent launch) ----------------
+/* ---- Mixed-length batched decoding (one persistent sweep) ------------------
  * Several batches, each with its own code (any supported N and rate), schedule
- * and buffers, decoded by one launch whose CTAs drain the batches in order
- * (each CTA re-shapes its frame slots for each batch's N).  Results are those
- * of bp_decode on each batch alone (same frame ids, same arithmetic).
- * Batches are processed in the order given: put the longest work first.
- * Scaled min-sum only (fkind 0). */
+ * and buffers.  Each batch runs the kernel bp_decode runs for its length; the
+ * launches after the first are programmatic dependent launches, and every
+ * decoder kernel lets its dependent start as soon as it has started itself,
+ * so a batch's CTAs take the SMs that the previous batch's CTAs leave while
+ * its last frames finish: one persistent sweep over all batches, without the
+ * tail of each separate launch.  Results are those of bp_decode on each batch
+ * alone (same frame ids, same arithmetic).  Batches run in the order given:
+ * put the longest work first.  Not in the paper (a throughput feature). */
 #define PC_MAX_BATCHES 64
 
 typedef struct {
@@ -210,21 +213,21 @@ typedef struct {
     uint8_t* d_crc_ok;        /* B */
 } pc_batch;
 
-/* Bytes of the device descriptor table of n_batches batches. */
+/* Bytes of the host launch table of n_batches batches. */
 int bp_mixed_table_size(int32_t n_batches, size_t* bytes);
-/* Writes the descriptor table of the batches (code tables, schedules,
- * buffer pointers, slot counts for the current device) into host memory
- * h_table; the caller copies it to device memory once and passes that copy
- * to bp_decode_mixed.  Host only (reads the current device's limits). */
+/* Validates the batches and writes, into caller-owned host memory h_table,
+ * each batch's kernel parameters (code tables, schedule, buffer pointers) and
+ * launch geometry for the current device.  Returns PC_EINVAL for an invalid
+ * batch, PC_ENOMEM when bytes is too small; queries the device only after
+ * every batch is valid. */
 int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes);
 /* Bytes of device workspace of bp_decode_mixed (one frame counter per batch). */
 int bp_mixed_workspace_size(int32_t n_batches, size_t* bytes);
-/* Decodes all batches with one kernel launch (after clearing the counters
- * in d_workspace).  d_table: the uploaded output of bp_mixed_prepare for the
- * same batches, 16-byte aligned.  Enqueues only a memset and a launch, so it
- * can be captured in a CUDA graph (make one uncaptured call first). */
-int bp_decode_mixed(const pc_batch* batches, int32_t n_batches, void* d_table, void* d_workspace,
-                    void* stream);
+/* Decodes all batches of a table written by bp_mixed_prepare (PC_EINVAL for
+ * anything else): clears the counters in d_workspace (256-byte aligned), then
+ * enqueues one launch per non-empty batch on the stream.  Enqueues only
+ * device work, so the call can be captured in a CUDA graph. */
+int bp_decode_mixed(const void* h_table, int32_t n_batches, void* d_workspace, void* stream);
 
 /* bp_decode for callers that cannot allocate device memory while they decode,
  * such as real-time signal-processing pipelines that allocate everything at

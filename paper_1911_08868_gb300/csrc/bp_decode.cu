@@ -113,10 +113,10 @@ int occupancy2_of(int n, const LaunchGeom& g, int fk)
     return occ;
 }
 
-cudaError_t launch2_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st)
+cudaError_t launch2_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st, bool pdl)
 {
     cudaError_t e = cudaSuccess;
-#define PCBP_LAUNCH2(k) e = bp2_launch_##k(P, g, fk, st)
+#define PCBP_LAUNCH2(k) e = bp2_launch_##k(P, g, fk, st, pdl)
     PCBP_SWITCH_N(n, PCBP_LAUNCH2)
 #undef PCBP_LAUNCH2
     return e;
@@ -142,13 +142,13 @@ int occupancy3_of(int n, const LaunchGeom& g, int fk)
     }
 }
 
-cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st)
+cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st, bool pdl)
 {
     switch (n) {
-        case 8: return bp3_launch_8(P, g, fk, st);
-        case 9: return bp3_launch_9(P, g, fk, st);
-        case 10: return bp3_launch_10(P, g, fk, st);
-        default: return bp3_launch_11(P, g, fk, st);
+        case 8: return bp3_launch_8(P, g, fk, st, pdl);
+        case 9: return bp3_launch_9(P, g, fk, st, pdl);
+        case 10: return bp3_launch_10(P, g, fk, st, pdl);
+        default: return bp3_launch_11(P, g, fk, st, pdl);
     }
 }
 
@@ -203,8 +203,9 @@ int plan_launch(const pc_code* c, int64_t B, bool trace, int fk, LaunchGeom* g)
     return PC_OK;
 }
 
-// Stage-grouped kernel: as many slots as shared memory and the block limit allow.
-int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
+// Stage-grouped kernel: as many slots as shared memory and the block limit
+// allow (at most slots_req when that is positive).
+int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g, int slots_req = 0)
 {
     DeviceInfo di;
     int rc = device_info(&di);
@@ -216,6 +217,7 @@ int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
     if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(di.smem_optin) - tab) / slot);
     slots = std::max(1, std::min(slots, max_slots));
+    if (slots_req > 0) slots = std::min(slots, slots_req);
     g->slots = slots;
     g->smem = tab + size_t(slots) * slot;
     g->grid = 1;
@@ -229,7 +231,7 @@ int plan_launch2(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
 // TMEM kernel: slots as for the stage-grouped kernel, then at least half an
 // SM's shared memory per CTA, so that one CTA per SM holds all 512 TMEM
 // columns and no allocation ever waits for another CTA.
-int plan_launch3(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
+int plan_launch3(const pc_code* c, int64_t B, int fk, LaunchGeom* g, int slots_req = 0)
 {
     DeviceInfo di;
     int rc = device_info(&di);
@@ -242,6 +244,7 @@ int plan_launch3(const pc_code* c, int64_t B, int fk, LaunchGeom* g)
     if (tab + slot > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(di.smem_optin) - tab) / slot);
     slots = std::max(1, std::min(slots, max_slots));
+    if (slots_req > 0) slots = std::min(slots, slots_req);
     g->slots = slots;
     g->smem = std::max(tab + size_t(slots) * slot, size_t(di.smem_per_sm) / 2 + 1024);
     if (g->smem > size_t(di.smem_optin)) return PC_EUNSUPPORTED;
@@ -271,6 +274,30 @@ int validate_events(const pc_code* c, const pc_event* ev, int n_ev)
     return PC_OK;
 }
 
+// Kernel parameters of one batch (no device calls).
+void fill_params(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters, int64_t B,
+                 uint32_t* d_bits, int32_t* d_iters, uint8_t* d_crc_ok, BpParams* P)
+{
+    std::memset(P, 0, sizeof(BpParams));
+    build_dev_code(code, &P->code);
+    build_dev_sched(sched, &P->sched);
+    P->llr = d_llr;
+    P->bits = d_bits;
+    P->iters = d_iters;
+    P->crc_ok = d_crc_ok;
+    P->B = B;
+    P->max_iters = max_iters;
+    P->job.S = P->sched;
+    P->job.llr = d_llr;
+    P->job.bits = d_bits;
+    P->job.iters = d_iters;
+    P->job.crc_ok = d_crc_ok;
+    P->job.B = B;
+    P->job.max_iters = max_iters;
+    P->job.K = code->K;
+    P->job.r = code->crc_len;
+}
+
 int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters, int64_t B,
                   bool trace, const pc_event* h_events, int32_t n_events, float* d_dump, uint32_t* d_bits,
                   int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace, void* stream)
@@ -292,9 +319,7 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
         }
     }
     std::unique_ptr<BpParams> P(new BpParams);
-    std::memset(P.get(), 0, sizeof(BpParams));
-    build_dev_code(code, &P->code);
-    build_dev_sched(sched, &P->sched);
+    fill_params(code, d_llr, sched, max_iters, B, d_bits, d_iters, d_crc_ok, P.get());
     if (trace && h_events) {
         P->sched.n_explicit = n_events;
         for (int k = 0; k < n_events; ++k) {
@@ -304,23 +329,9 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
             for (int i = 0; i < 16; ++i) P->events[k].order[i] = (int8_t)(i < h_events[k].range ? h_events[k].order[i] : i);
         }
     }
-    P->llr = d_llr;
-    P->bits = d_bits;
-    P->iters = d_iters;
-    P->crc_ok = d_crc_ok;
+    P->job.S = P->sched;         // after the explicit events
     P->counter = reinterpret_cast<unsigned long long*>(d_workspace);
     P->dump = d_dump;
-    P->B = B;
-    P->max_iters = max_iters;
-    P->job.S = P->sched;
-    P->job.llr = d_llr;
-    P->job.bits = d_bits;
-    P->job.iters = d_iters;
-    P->job.crc_ok = d_crc_ok;
-    P->job.B = B;
-    P->job.max_iters = max_iters;
-    P->job.K = code->K;
-    P->job.r = code->crc_len;
 
     LaunchGeom g;
     const bool tmem = !trace && use_tmem_kernel(code->n);
@@ -331,8 +342,8 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
     const cudaError_t e = trace  ? launch_of(code->n, *P, g, true, sched->fkind, st)
-                          : tmem ? launch3_of(code->n, *P, g, sched->fkind, st)
-                                 : launch2_of(code->n, *P, g, sched->fkind, st);
+                          : tmem ? launch3_of(code->n, *P, g, sched->fkind, st, false)
+                                 : launch2_of(code->n, *P, g, sched->fkind, st, false);
     if (e != cudaSuccess) return PC_ECUDA;
     return PC_OK;
 }
@@ -416,6 +427,113 @@ extern "C" int bp_decode(const pc_code* code, const float* d_llr, const pc_sched
 {
     return decode_common(code, d_llr, sched, max_iters, B, false, nullptr, 0, nullptr, d_bits, d_iters, d_crc_ok,
                          d_workspace, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-length batches: each batch is launched with the kernel bp_decode
+// runs for its length, all on one stream; every launch after the first is a
+// programmatic dependent launch and the kernels trigger their dependents as
+// they start, so a batch's CTAs take the SMs that the previous batch's CTAs
+// leave while its last frames finish: one persistent sweep over all the
+// batches, with no per-size tail.
+namespace pcbp {
+namespace {
+
+constexpr uint32_t kMixedMagic = 0x70636278u;
+
+struct MixedEntry {
+    BpParams P;
+    LaunchGeom g;
+    int32_t n, tmem, fkind;
+    uint32_t magic;
+};
+
+int validate_batch(const pc_batch& b)
+{
+    if (!b.code) return PC_EINVAL;
+    int rc = validate_code(b.code);
+    if (rc != PC_OK) return rc;
+    rc = validate_sched(b.code, &b.sched);
+    if (rc != PC_OK) return rc;
+    if (b.max_iters < 0 || b.B < 0 || b.slots < 0) return PC_EINVAL;
+    if (b.B > 0) {
+        if (!b.d_llr || !b.d_bits || !b.d_iters || !b.d_crc_ok) return PC_EINVAL;
+        if (reinterpret_cast<uintptr_t>(b.d_llr) & 15u) return PC_EINVAL;
+    }
+    return PC_OK;
+}
+
+}  // namespace
+}  // namespace pcbp
+
+extern "C" int bp_mixed_table_size(int32_t n_batches, size_t* bytes)
+{
+    if (n_batches < 0 || n_batches > PC_MAX_BATCHES || !bytes) return PC_EINVAL;
+    *bytes = sizeof(MixedEntry) * size_t(n_batches);
+    return PC_OK;
+}
+
+extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes)
+{
+    if (n_batches < 0 || n_batches > PC_MAX_BATCHES || (n_batches > 0 && (!batches || !h_table))) return PC_EINVAL;
+    if (bytes < sizeof(MixedEntry) * size_t(n_batches)) return PC_ENOMEM;
+    for (int i = 0; i < n_batches; ++i) {
+        const int rc = validate_batch(batches[i]);
+        if (rc != PC_OK) return rc;
+    }
+    for (int i = 0; i < n_batches; ++i) {
+        const pc_batch& b = batches[i];
+        std::unique_ptr<MixedEntry> m(new MixedEntry);
+        std::memset(m.get(), 0, sizeof(MixedEntry));
+        fill_params(b.code, b.d_llr, &b.sched, b.max_iters, b.B, b.d_bits, b.d_iters, b.d_crc_ok, &m->P);
+        m->n = b.code->n;
+        m->fkind = b.sched.fkind;
+        m->tmem = use_tmem_kernel(b.code->n) ? 1 : 0;
+        if (b.B > 0) {
+            const int rc = m->tmem ? plan_launch3(b.code, b.B, b.sched.fkind, &m->g, b.slots)
+                                   : plan_launch2(b.code, b.B, b.sched.fkind, &m->g, b.slots);
+            if (rc != PC_OK) return rc;
+            m->P.slots = m->g.slots;
+        }
+        m->magic = kMixedMagic;
+        std::memcpy(static_cast<MixedEntry*>(h_table) + i, m.get(), sizeof(MixedEntry));
+    }
+    return PC_OK;
+}
+
+extern "C" int bp_mixed_workspace_size(int32_t n_batches, size_t* bytes)
+{
+    if (n_batches < 0 || n_batches > PC_MAX_BATCHES || !bytes) return PC_EINVAL;
+    *bytes = (sizeof(unsigned long long) * size_t(n_batches) + 255) & ~size_t(255);
+    if (*bytes == 0) *bytes = 256;
+    return PC_OK;
+}
+
+extern "C" int bp_decode_mixed(const void* h_table, int32_t n_batches, void* d_workspace, void* stream)
+{
+    if (n_batches < 0 || n_batches > PC_MAX_BATCHES) return PC_EINVAL;
+    if (n_batches == 0) return PC_OK;
+    if (!h_table || !d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return PC_EINVAL;
+    std::unique_ptr<MixedEntry> m(new MixedEntry);
+    for (int i = 0; i < n_batches; ++i) {
+        std::memcpy(m.get(), static_cast<const MixedEntry*>(h_table) + i, sizeof(MixedEntry));
+        if (m->magic != kMixedMagic) return PC_EINVAL;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    size_t ws = 0;
+    bp_mixed_workspace_size(n_batches, &ws);
+    if (cudaMemsetAsync(d_workspace, 0, ws, st) != cudaSuccess) return PC_ECUDA;
+    bool first = true;
+    for (int i = 0; i < n_batches; ++i) {
+        std::memcpy(m.get(), static_cast<const MixedEntry*>(h_table) + i, sizeof(MixedEntry));
+        if (m->P.B == 0) continue;
+        m->P.counter = reinterpret_cast<unsigned long long*>(d_workspace) + i;
+        const cudaError_t e = m->tmem ? launch3_of(m->n, m->P, m->g, m->fkind, st, !first)
+                                      : launch2_of(m->n, m->P, m->g, m->fkind, st, !first);
+        if (e != cudaSuccess) return PC_ECUDA;
+        first = false;
+    }
+    return PC_OK;
 }
 
 extern "C" int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters,

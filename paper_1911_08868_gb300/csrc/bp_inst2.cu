@@ -20,14 +20,29 @@ namespace {
 constexpr int KBSEL = PCBP_LOGN < PCBP_KB ? PCBP_LOGN : PCBP_KB;
 using Geo = G2<PCBP_LOGN, KBSEL>;
 
+// pdl: programmatic dependent launch, the grid may start while the previous
+// kernel of the stream still runs (for independent batches).
 template <int FK>
-cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st)
+cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st, bool pdl)
 {
     auto kern = bp_decode_grouped_kernel<PCBP_LOGN, KBSEL, FK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
     if (e != cudaSuccess) return e;
-    kern<<<g.grid, g.slots * Geo::T, g.smem, st>>>(P);
-    return cudaGetLastError();
+    if (!pdl) {
+        kern<<<g.grid, g.slots * Geo::T, g.smem, st>>>(P);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(g.grid));
+    cfg.blockDim = dim3(unsigned(g.slots * Geo::T));
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, P);
 }
 
 template <int FK>
@@ -57,9 +72,10 @@ int PCBP_CAT(bp2_occupancy_, PCBP_LOGN)(const LaunchGeom& g, int fkind)
     return fkind ? occupancy<1>(g) : occupancy<0>(g);
 }
 
-cudaError_t PCBP_CAT(bp2_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st)
+cudaError_t PCBP_CAT(bp2_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st,
+                                             bool pdl)
 {
-    return fkind ? launch_variant<1>(P, g, st) : launch_variant<0>(P, g, st);
+    return fkind ? launch_variant<1>(P, g, st, pdl) : launch_variant<0>(P, g, st, pdl);
 }
 
 }  // namespace pcbp

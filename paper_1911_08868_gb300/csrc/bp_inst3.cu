@@ -20,14 +20,29 @@ namespace {
 constexpr int KB = PCBP_KB3;   // 2^KB positions per thread
 using Geo = G3<PCBP_LOGN, KB>;
 
+// pdl: programmatic dependent launch, the grid may start while the previous
+// kernel of the stream still runs (for independent batches).
 template <int FK>
-cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st)
+cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st, bool pdl)
 {
     auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
     if (e != cudaSuccess) return e;
-    kern<<<g.grid, g.slots * Geo::T, g.smem, st>>>(P);
-    return cudaGetLastError();
+    if (!pdl) {
+        kern<<<g.grid, g.slots * Geo::T, g.smem, st>>>(P);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(g.grid));
+    cfg.blockDim = dim3(unsigned(g.slots * Geo::T));
+    cfg.dynamicSmemBytes = g.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, P);
 }
 
 template <int FK>
@@ -55,16 +70,17 @@ void PCBP_CAT(bp3_shape_, PCBP_LOGN)(int* threads_per_slot_out, size_t* slot_byt
     *max_slots_out = slots;
 }
 
-void PCBP_CAT(bp3_tables_, PCBP_LOGN)(int N, int K, size_t* bytes) { *bytes = tmem_table_bytes(N, K); }
+void PCBP_CAT(bp3_tables_, PCBP_LOGN)(int N, int K, size_t* bytes) { *bytes = tmem_cta_bytes<PCBP_LOGN, KB>(N, K); }
 
 int PCBP_CAT(bp3_occupancy_, PCBP_LOGN)(const LaunchGeom& g, int fkind)
 {
     return fkind ? occupancy<1>(g) : occupancy<0>(g);
 }
 
-cudaError_t PCBP_CAT(bp3_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st)
+cudaError_t PCBP_CAT(bp3_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st,
+                                             bool pdl)
 {
-    return fkind ? launch_variant<1>(P, g, st) : launch_variant<0>(P, g, st);
+    return fkind ? launch_variant<1>(P, g, st, pdl) : launch_variant<0>(P, g, st, pdl);
 }
 
 }  // namespace pcbp

@@ -726,6 +726,8 @@ __device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long 
 template <int LOGN, int KB, int FK>
 __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_grouped_kernel(const __grid_constant__ BpParams P)
 {
+    // a kernel launched after this one may start as soon as SMs free up
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
     load_code_tables(P.code, smem);
     __syncthreads();

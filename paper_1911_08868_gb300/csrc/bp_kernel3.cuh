@@ -193,6 +193,7 @@ struct Ctl3 {
     uint2 cmask[LOGN];
     alignas(16) short swoff[LOGN][2][1 << KB];
     unsigned crc_part[3];    // CRC residue of iteration it, accumulated in crc_part[it % 3]
+    unsigned pad_;
 };
 
 // ---------------------------------------------------------------------------
@@ -384,6 +385,39 @@ __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float 
     }
 }
 
+// Shared memory ahead of the frame slots: code tables, then the control
+// block of the no-event partition (built once per CTA, copied into a slot
+// whose previous frame switched partitions).
+template <int LOGN, int KB>
+__host__ __device__ inline size_t tmem_cta_bytes(int N, int K)
+{
+    return tmem_table_bytes(N, K) + align16(sizeof(Ctl3<LOGN, KB>));
+}
+
+// The no-event control block (one thread).
+template <int LOGN, int KB>
+__device__ __noinline__ void build_template(Ctl3<LOGN, KB>* c, const unsigned char* s_swz)
+{
+    c->g.frame = 0;
+    c->g.have_ev = 0;
+    c->g.have_prev = 0;
+    c->g.ev_level = 0;
+    c->g.ev_range = 0;
+    c->g.ev_blk = -1;
+    c->g.pv_level = 0;
+    c->g.pv_range = 0;
+    c->g.pv_blk = -1;
+    c->g.next_inc = 0;
+    c->g.crc_res = 0;
+    c->g.g_ok = 0;
+    c->crc_part[0] = 0u;
+    c->crc_part[1] = 0u;
+    c->crc_part[2] = 0u;
+    signed char none[16];
+    build_groups<LOGN, KB>(&c->g, s_swz, LOGN, false, 0, 0, 0, none, true);
+    pack_groups<LOGN, KB>(c);
+}
+
 template <int LOGN, int KB, int FK>
 __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long long* counter, unsigned char* smem,
                                             uint32_t tm_base)
@@ -413,7 +447,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int warp = tid >> 5;
     constexpr size_t ctl_bytes = align16(sizeof(Ctl));
     constexpr size_t slot_sz = ctl_bytes + align16(size_t(2 * NW * 4)) + size_t(2 * NPL) * N * 4;
-    unsigned char* sbase = smem + tmem_table_bytes(N, K) + size_t(slot) * slot_sz;
+    const Ctl* tmpl = reinterpret_cast<const Ctl*>(smem + tmem_table_bytes(N, K));
+    unsigned char* sbase = smem + tmem_cta_bytes<LOGN, KB>(N, K) + size_t(slot) * slot_sz;
     Ctl* ctl = reinterpret_cast<Ctl*>(sbase);
     uint32_t* dec = reinterpret_cast<uint32_t*>(sbase + ctl_bytes);
     uint32_t* xh = dec + NW;
@@ -568,20 +603,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 
         for (int i = tid; i < NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = tid; i < NW; i += T) dec[i] = 0u;
-        if (tid == 0) {
-            ctl->g.have_ev = 0;
-            ctl->g.have_prev = 0;
-            ctl->g.ev_level = 0;
-            ctl->g.ev_range = 0;
-            ctl->g.ev_blk = -1;
-            ctl->crc_part[0] = 0u;
-            ctl->crc_part[1] = 0u;
-            ctl->crc_part[2] = 0u;
-            if (!fresh) {
-                signed char none[16];
-                build_groups<LOGN, KB>(&ctl->g, s_swz, n, false, 0, 0, 0, none, true);
-                pack_groups<LOGN, KB>(ctl);
+        if (fresh) {
+            // the partition is still the no-event one; only the residues restart
+            if (tid == 0) {
+                ctl->crc_part[0] = 0u;
+                ctl->crc_part[1] = 0u;
+                ctl->crc_part[2] = 0u;
             }
+        } else {
+            static_assert(sizeof(Ctl) % 16 == 0, "control block copied in 16-byte words");
+            for (int i = tid; i < int(sizeof(Ctl) / 16); i += T)
+                reinterpret_cast<int4*>(ctl)[i] = reinterpret_cast<const int4*>(tmpl)[i];
         }
         sync();
         if (fresh) restart_partition(llr_f);
@@ -970,9 +1002,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 template <int LOGN, int KB, int FK>
 __global__ void __launch_bounds__(tmem_max_threads<LOGN>(), 1) bp_decode_tmem_kernel(const __grid_constant__ BpParams P)
 {
+    // a kernel launched after this one may start as soon as SMs free up
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ uint32_t s_tm;
     load_code_tables3(P.code, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int N = P.code.N, K = P.code.K;
+        build_template<LOGN, KB>(reinterpret_cast<Ctl3<LOGN, KB>*>(smem + tmem_table_bytes(N, K)),
+                                 smem + tmem_table_bytes(N, K) - kSwzTableBytes);
+    }
     if (threadIdx.x < 32) {
         const uint32_t dst = uint32_t(__cvta_generic_to_shared(&s_tm));
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst), "n"(kTmemCols)

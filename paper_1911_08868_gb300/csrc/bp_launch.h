@@ -23,7 +23,7 @@ struct LaunchGeom {
     cudaError_t bp_launch_##n(const BpParams& P, const LaunchGeom& g, bool trace, int fkind, cudaStream_t st); \
     void bp2_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out);            \
     int bp2_occupancy_##n(const LaunchGeom& g, int fkind);                                                \
-    cudaError_t bp2_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st);
+    cudaError_t bp2_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st, bool pdl);
 
 PCBP_DECLARE_LEN(3)
 PCBP_DECLARE_LEN(4)
@@ -41,7 +41,7 @@ PCBP_DECLARE_LEN(11)
     void bp3_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out); \
     void bp3_tables_##n(int N, int K, size_t* bytes);                                          \
     int bp3_occupancy_##n(const LaunchGeom& g, int fkind);                                     \
-    cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st);
+    cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st, bool pdl);
 
 PCBP_DECLARE_LEN3(8)
 PCBP_DECLARE_LEN3(9)

@@ -70,7 +70,7 @@ _lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C
 _lib.bp_mixed_table_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_mixed_prepare.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, C.c_size_t]
 _lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
-_lib.bp_decode_mixed.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, _vp, _vp]
+_lib.bp_decode_mixed.argtypes = [_vp, C.c_int32, _vp, _vp]
 _lib.wbp_weights_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_size_t)]
 _lib.wbp_ckpt_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]
 _lib.wbp_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
@@ -301,19 +301,18 @@ def bp_mixed_prepare(batches, h_table):
                                                      C.sizeof(h_table)))
 
 
-def bp_decode_mixed(batches, d_table, workspace, stream=None):
-    arr = (PcBatch * len(batches))(*batches)
-    _check("bp_decode_mixed", _lib.bp_decode_mixed(arr, len(batches), _ptr(d_table), _ptr(workspace),
+def bp_decode_mixed(h_table, n_batches, workspace, stream=None):
+    _check("bp_decode_mixed", _lib.bp_decode_mixed(C.cast(h_table, C.c_void_p), n_batches, _ptr(workspace),
                                                    _stream(stream)))
 
 
 class MixedDecoder:
-    """One persistent launch over several batches of different codes.
+    """Batches of different codes decoded in one persistent sweep (bp_decode_mixed).
 
     parts: list of (code, sched, max_iters, llr [B, N] CUDA float32 tensor, slots).  Output
-    tensors per batch are allocated here (`bits[i]`, `iters[i]`, `crc_ok[i]`); the device
-    descriptor table is prepared once and uploaded, so `__call__` only enqueues a memset and
-    one kernel (it can be captured in a CUDA graph after a first uncaptured call)."""
+    tensors per batch are allocated here (`bits[i]`, `iters[i]`, `crc_ok[i]`); the launch
+    table is prepared once, so `__call__` only enqueues a memset and one launch per batch (it
+    can be captured in a CUDA graph after a first uncaptured call)."""
 
     def __init__(self, parts, device="cuda"):
         import torch
@@ -338,13 +337,13 @@ class MixedDecoder:
                                                         ok.data_ptr())
             self.batches.append(b)
         nb = len(self.batches)
-        h = (C.c_char * max(bp_mixed_table_size(nb), 1))()
-        bp_mixed_prepare(self.batches, h)
-        self.table = torch.frombuffer(bytearray(h), dtype=torch.uint8).to(self.device)
+        with torch.cuda.device(self.device):
+            self.table = (C.c_char * max(bp_mixed_table_size(nb), 1))()
+            bp_mixed_prepare(self.batches, self.table)
         self.workspace = torch.zeros(bp_mixed_workspace_size(nb), dtype=torch.uint8, device=self.device)
 
     def __call__(self, stream=None):
-        bp_decode_mixed(self.batches, self.table, self.workspace, stream)
+        bp_decode_mixed(self.table, len(self.batches), self.workspace, stream)
         return self.bits, self.iters, self.crc_ok
 
 

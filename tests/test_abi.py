@@ -164,14 +164,17 @@ def test_mixed_entry_points_validate_on_the_host(pcbp):
     nob.d_llr = None
     arr = (pcbp.PcBatch * 1)(nob)
     assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
+    # a valid batch (box-plus included) gets past validation to the device query
     bx = pcbp.PcBatch.from_buffer_copy(b)
     bx.sched = pcbp.sched(fkind=1)
     arr = (pcbp.PcBatch * 1)(bx)
-    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EUNSUPPORTED
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_ECUDA
     arr = (pcbp.PcBatch * 1)(b)
     assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), 8) == pcbp.PC_ENOMEM
     assert pcbp._lib.bp_mixed_prepare(arr, 65, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
-    assert pcbp._lib.bp_decode_mixed(arr, 0, None, None, None) == pcbp.PC_OK
-    assert pcbp._lib.bp_decode_mixed(arr, 1, None, C.c_void_p(4096), None) == pcbp.PC_EINVAL
-    bad_arr = (pcbp.PcBatch * 1)(bad)
-    assert pcbp._lib.bp_decode_mixed(bad_arr, 1, C.c_void_p(4096), C.c_void_p(4096), None) == pcbp.PC_EINVAL
+    # decode: nothing to do, missing workspace, a table bp_mixed_prepare did not write
+    assert pcbp._lib.bp_decode_mixed(C.cast(h, C.c_void_p), 0, None, None) == pcbp.PC_OK
+    assert pcbp._lib.bp_decode_mixed(C.cast(h, C.c_void_p), 1, None, None) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_decode_mixed(None, 1, C.c_void_p(4096), None) == pcbp.PC_EINVAL
+    zeros = (C.c_char * pcbp.bp_mixed_table_size(1))()
+    assert pcbp._lib.bp_decode_mixed(C.cast(zeros, C.c_void_p), 1, C.c_void_p(4096), None) == pcbp.PC_EINVAL

@@ -101,3 +101,20 @@ def test_mixed_graph_replay_and_slot_override(pcbp, oracle):
     torch.cuda.synchronize()
     for k in range(len(parts)):
         assert torch.equal(b1[k], first[k][0]) and torch.equal(i1[k], first[k][1]) and torch.equal(o1[k], first[k][2])
+
+
+def test_mixed_box_plus_and_min_sum_batches(pcbp, oracle):
+    """Box-plus and scaled min-sum batches in one sweep equal bp_decode on each."""
+    import torch
+
+    dev = gpu_device()
+    parts, _ = make_parts(pcbp, oracle, dev, [(1024, 0.5), (256, 0.5), (128, 0.5)], 200, seed=91)
+    bx = pcbp.sched(mode=1, rho_range_fixed=3, P_level=7, N_min=5, T0=5, seed=5, stop_kind=1, fkind=1)
+    parts[1] = (parts[1][0], bx, 60, parts[1][3], 0)
+    md = pcbp.MixedDecoder(parts, dev)
+    bits, iters, ok = md()
+    torch.cuda.synchronize()
+    want = per_batch(pcbp, parts)
+    for i in range(len(parts)):
+        assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1])
+        assert torch.equal(ok[i], want[i][2])
