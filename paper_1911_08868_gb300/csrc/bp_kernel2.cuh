@@ -223,61 +223,22 @@ __device__ __forceinline__ unsigned char* load_code_tables(const DevCode& code, 
     return s_swz + kSwzTableBytes;
 }
 
-// G-matrix test for a length known only at run time (one warp); see g_check.
-__device__ __forceinline__ bool g_check_rt(const uint32_t* dec, const uint32_t* xh, int lane, int n)
-{
-    const int NW = n >= 5 ? 1 << (n - 5) : 1;
-    uint32_t v[2];
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int w = lane + 32 * e;
-        v[e] = w < NW ? dec[w] : 0u;
-    }
-    const uint32_t masks[5] = {0x55555555u, 0x33333333u, 0x0F0F0F0Fu, 0x00FF00FFu, 0x0000FFFFu};
-    for (int p = 0; p < (n < 5 ? n : 5); ++p)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) v[e] ^= (v[e] >> (1 << p)) & masks[p];
-    for (int p = 5; p < n; ++p) {
-        const int q = p - 5;
-        if (q < 5) {
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const uint32_t other = __shfl_xor_sync(0xffffffffu, v[e], 1 << q);
-                if (!((lane >> q) & 1)) v[e] ^= other;
-            }
-        } else {
-            v[0] ^= v[1];
-        }
-    }
-    bool ok = true;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const int w = lane + 32 * e;
-        if (w < NW) ok = ok && (v[e] == xh[w]);
-    }
-    return __all_sync(0xffffffffu, ok);
-}
-
-// Decodes frames of one job until the counter passes B (J may live in
-// parameter or global memory: it is read where it is).  Threads
+// Decodes frames of one job until the counter passes B.  Threads
 // [0, nslots * T) take part, in slots of T threads; the code tables are
 // already in shared memory (load_code_tables) and visible to all of them.
-// LOGN = 0: the length comes from n_rt at run time (one body for every
-// length); otherwise every geometric quantity below is a constant.
 template <int LOGN, int KB, int FK>
-__device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long long* counter,
-                                               unsigned char* smem, int n_rt)
+__device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long long* counter, unsigned char* smem)
 {
-    constexpr int CL = LOGN ? LOGN : kMaxLogN;
+    constexpr int CL = LOGN;
     using Ctl = GroupCtl<CL, KB>;
-    const int n = LOGN ? LOGN : n_rt;
-    const int N = 1 << n;
+    constexpr int n = LOGN;
+    constexpr int N = 1 << n;
     constexpr int E = 1 << KB;
-    const int TA = N / E;
-    const int T = TA < 32 ? 32 : TA;
-    const int NW = N >= 32 ? N / 32 : 1;
-    const int NWARP = T / 32;
-    const int NPL = n - 1;
+    constexpr int TA = N / E;
+    constexpr int T = TA < 32 ? 32 : TA;
+    constexpr int NW = N >= 32 ? N / 32 : 1;
+    constexpr int NWARP = T / 32;
+    constexpr int NPL = n - 1;
 
     const int r = J.r;
     const int K = J.K;
@@ -623,7 +584,7 @@ __device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long 
                 if (S.stop_kind & 1) ok = res == 0;
                 if (want_g) {
                     if (warp == 0) {
-                        const bool gok = LOGN ? g_check<(LOGN ? LOGN : 3)>(dec, xh, lane) : g_check_rt(dec, xh, lane, n);
+                        const bool gok = g_check<LOGN>(dec, xh, lane);
                         if (lane == 0) ctl->g_ok = gok ? 1 : 0;
                     }
                     sync();
@@ -731,7 +692,7 @@ __global__ void __launch_bounds__(grouped_max_threads<KB>(), 1) bp_decode_groupe
     extern __shared__ __align__(16) unsigned char smem[];
     load_code_tables(P.code, smem);
     __syncthreads();
-    grouped_frames<LOGN, KB, FK>(P.job, P.counter, smem, LOGN);
+    grouped_frames<LOGN, KB, FK>(P.job, P.counter, smem);
 }
 
 }  // namespace pcbp
