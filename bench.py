@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-wbp", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     return ap.parse_args()
 
 
@@ -297,6 +298,59 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
                         "max 300 it, CRC-8 (N<=256) / CRC-24"}
 
 
+VARIANT_FRAMES = 1 << 17
+VARIANTS = {
+    # the benchmark schedule at this frame count, for reference
+    "ppbp_s4_t10": dict(SCHED),
+    # FP-BP: q_max = 10 trellises of 100 iterations each (a full-order event and a whole-graph reset)
+    "fpbp_q10_t100": dict(mode=2, it_reset_full=100, q_max=10, stop_from=1, stop_kind=1, alpha=0.9375, seed=3),
+    # BP on the original graph only
+    "plain_bp": dict(mode=0, stop_from=1, stop_kind=1, alpha=0.9375, seed=3),
+    # unscaled min-sum, as the paper simulates
+    "ppbp_alpha1": dict(SCHED, alpha=1.0),
+    # CRC and G-matrix stop together
+    "ppbp_crc_and_g": dict(SCHED, stop_kind=3),
+    # exact box-plus f
+    "ppbp_boxplus": dict(SCHED, fkind=1),
+}
+VARIANT_MAX_ITERS = {"fpbp_q10_t100": 1000}
+
+
+def run_variants(pcbp, inputs, dev, warmup):
+    """Throughput, FER and mean iterations of the other schedules of the same code on the same
+    2^17 frames (Eb/N0 3.0 dB): FP-BP, plain BP, unscaled min-sum, CRC + G-matrix stop, box-plus."""
+    import torch
+
+    B = VARIANT_FRAMES
+    code = pcbp.pc_construct(N, K, R_CRC, POLY)
+    gen = torch.Generator(device=dev).manual_seed(777)
+    pay = inputs.payload_torch(gen, B, K - R_CRC, dev)
+    x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+    pcbp.pc_encode(code, pay, x)
+    llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(EBN0, K, R_CRC, N)).contiguous()
+    del x
+    out = {"frames": B, "ebn0_db": EBN0}
+    for name, kw in VARIANTS.items():
+        max_iters = VARIANT_MAX_ITERS.get(name, MAX_ITERS)
+        dec = pcbp.Decoder(code, pcbp.sched(**kw), max_iters, dev)
+        for _ in range(max(1, min(warmup, 2))):
+            dec(llr)
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        dec(llr)
+        t1.record()
+        torch.cuda.synchronize()
+        ms = t0.elapsed_time(t1)
+        got = pcbp.unpack_bits(dec.bits, K)[:, : K - R_CRC]
+        errors = int((got != pay).any(dim=1).sum().item())
+        out[name] = {"gbit_s": B * (K - R_CRC) / (ms / 1e3) / 1e9, "ms": ms, "max_iters": max_iters,
+                     "fer": errors / B, "fer_ci95": wilson(errors, B),
+                     "mean_iters": float(dec.iters.double().mean().item())}
+    return out
+
+
 def wbp_loss(logits, bits):
     import torch
 
@@ -516,6 +570,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_wbp:
         line["wbp"] = run_wbp(pcbp, inputs, dev, args.steps, args.warmup)
+
+    if rank == 0 and not args.no_variants:
+        line["variants"] = run_variants(pcbp, inputs, dev, args.warmup)
 
     if rank == 0 and not args.no_mixed:
         del dec
