@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-wbp", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="FER curves over Eb/N0 1.5..4.0 dB instead of the benchmark line")
+    ap.add_argument("--sweep-frames", type=int, default=1_000_000)
+    ap.add_argument("--sweep-oracle-frames", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -222,7 +226,8 @@ def mixed_sched(pcbp, n, seed):
 def run_mixed(pcbp, inputs, dev, steps, warmup):
     """2^20 frames, N uniform on {128..2048}, rate uniform on {1/4, 1/2, 3/4}, Eb/N0 uniform on
     [1, 4] dB per frame, PP-BP s=4 T=10: 15 per-size bp_decode launches against one
-    persistent mixed launch (slots from the autotuner), both also replayed from CUDA graphs."""
+    persistent mixed sweep (threads per frame and slots from the autotuner), both also replayed
+    from CUDA graphs."""
     import numpy as np
     import torch
 
@@ -231,7 +236,7 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
     rng = np.random.default_rng(7)
     classes = [(N, R) for N in MIXED_LENGTHS for R in MIXED_RATES]
     counts = rng.multinomial(MIXED_FRAMES, [1 / len(classes)] * len(classes))
-    slots = autotune.tune_slots(MIXED_LENGTHS, lambda n: mixed_sched(pcbp, n, 1), max_iters=MAX_ITERS, device=dev)
+    tuned = autotune.tune_launch(MIXED_LENGTHS, lambda n: mixed_sched(pcbp, n, 1), max_iters=MAX_ITERS, device=dev)
     gen = torch.Generator(device=dev).manual_seed(4321)
     parts, info_bits = [], 0
     order = sorted(range(len(classes)), key=lambda i: -classes[i][0] * counts[i])
@@ -247,7 +252,7 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
         llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0.cpu().numpy(), K, r, N)).contiguous()
         del x
         sch = mixed_sched(pcbp, N.bit_length() - 1, 1000 + ci)
-        parts.append((code, sch, MAX_ITERS, llr, slots[N]))
+        parts.append((code, sch, MAX_ITERS, llr, tuned[N]["slots"], tuned[N]["threads_per_frame"]))
         info_bits += B * (K - r)
     decs = [pcbp.Decoder(p[0], p[1], p[2], dev) for p in parts]
     md = pcbp.MixedDecoder(parts, dev)
@@ -293,7 +298,7 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
             "mixed_graph_ms": graphs["mixed"], "speedup": t_per / t_mix,
             "speedup_graphs": graphs["per_size"] / graphs["mixed"],
             "mixed_gbit_s": info_bits / (graphs["mixed"] / 1e3) / 1e9,
-            "slots": {str(k): v for k, v in slots.items()}, "outputs_identical": bool(same),
+            "tuned": {str(k): v for k, v in tuned.items()}, "outputs_identical": bool(same),
             "workload": "2^20 frames, N~U{128..2048}, R~U{1/4,1/2,3/4}, Eb/N0~U[1,4] dB, PP-BP s=4 T=10, "
                         "max 300 it, CRC-8 (N<=256) / CRC-24"}
 
@@ -349,6 +354,76 @@ def run_variants(pcbp, inputs, dev, warmup):
                      "fer": errors / B, "fer_ci95": wilson(errors, B),
                      "mean_iters": float(dec.iters.double().mean().item())}
     return out
+
+
+SWEEP_EBN0 = tuple(1.5 + 0.25 * i for i in range(11))
+SWEEP_SCHEDULES = {f"ppbp_s{s_}_t{t_}": dict(mode=1, rho_range_fixed=s_, P_level=9, N_min=t_, D=0, T0=t_, stop_from=1,
+                                             stop_kind=1, alpha=0.9375, seed=3)
+                   for s_ in (3, 4, 5) for t_ in (5, 10, 20)}
+SWEEP_SCHEDULES["fpbp_q10_t100"] = VARIANTS["fpbp_q10_t100"]
+SWEEP_SCHEDULES["plain_bp"] = VARIANTS["plain_bp"]
+SWEEP_ORACLE = ("ppbp_s4_t10", "fpbp_q10_t100")
+
+
+def run_sweep(args):
+    """FER and mean iterations of the PP-BP grid (s in {3,4,5}, T in {5,10,20}), FP-BP and plain BP
+    at Eb/N0 1.5..4.0 dB on the benchmark code; for the benchmark schedule and FP-BP, the oracle
+    decodes the first frames of every point too (same frame ids): its FER interval, and whether its
+    decisions and iteration counts equal the GPU's on those frames."""
+    import numpy as np
+    import torch
+
+    import oracle as O
+    from paper_1911_08868_gb300 import _build
+
+    _build.build()
+    from paper_1911_08868_gb300 import inputs, pcbp
+
+    dev = torch.device("cuda", 0)
+    B, Bo = args.sweep_frames, args.sweep_oracle_frames
+    code = pcbp.pc_construct(N, K, R_CRC, POLY)
+    _, fr = O.construct(N, K)
+    threads = O.max_threads()
+    rows = []
+    for ebn0 in SWEEP_EBN0:
+        gen = torch.Generator(device=dev).manual_seed(5000 + int(round(ebn0 * 100)))
+        pay = inputs.payload_torch(gen, B, K - R_CRC, dev)
+        x = torch.empty((B, N), dtype=torch.uint8, device=dev)
+        pcbp.pc_encode(code, pay, x)
+        llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0, K, R_CRC, N)).contiguous()
+        del x
+        sub_llr = llr[:Bo].cpu().numpy()
+        sub_pay = pay[:Bo].cpu().numpy()
+        for name, kw in SWEEP_SCHEDULES.items():
+            max_iters = VARIANT_MAX_ITERS.get(name, MAX_ITERS)
+            dec = pcbp.Decoder(code, pcbp.sched(**kw), max_iters, dev)
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record()
+            dec(llr)
+            t1.record()
+            torch.cuda.synchronize()
+            got = pcbp.unpack_bits(dec.bits, K)[:, : K - R_CRC]
+            errors = int((got != pay).any(dim=1).sum().item())
+            row = {"schedule": name, "ebn0_db": ebn0, "frames": B, "fer": errors / B, "errors": errors,
+                   "fer_ci95": wilson(errors, B), "mean_iters": float(dec.iters.double().mean().item()),
+                   "gbit_s": B * (K - R_CRC) / (t0.elapsed_time(t1) / 1e3) / 1e9}
+            if name in SWEEP_ORACLE:
+                os_ = O.Sched(**kw)
+                u, it, ok = O.decode_batch(fr, R_CRC, POLY, sub_llr, os_, max_iters, nthreads=threads)
+                ogot = O.info_bits(u, fr)[:, : K - R_CRC]
+                oerr = int((ogot != sub_pay).any(axis=1).sum())
+                oci = wilson(oerr, Bo)
+                gsub = got[:Bo].cpu().numpy()
+                gits = dec.iters[:Bo].cpu().numpy()
+                row["oracle"] = {"frames": Bo, "fer": oerr / Bo, "fer_ci95": oci, "mean_iters": float(it.mean()),
+                                 "identical_decisions": bool(np.array_equal(ogot, gsub)),
+                                 "identical_iterations": bool(np.array_equal(it, gits)),
+                                 "intervals_overlap": bool(oci[0] <= row["fer_ci95"][1] and row["fer_ci95"][0] <= oci[1])}
+            rows.append(row)
+        del llr, pay
+    print(json.dumps({"sweep": rows, "code": "N=1024 K=512 CRC-24 (0x1B2B117)", "data": "synthetic BPSK/AWGN",
+                      "oracle_cores": threads, "dtype": "f32"}), flush=True)
 
 
 def wbp_loss(logits, bits):
@@ -596,7 +671,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.sweep:
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

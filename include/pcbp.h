@@ -206,6 +206,10 @@ typedef struct {
     pc_sched sched;           /* frame b draws events with frame id sched.frame_base + b */
     int32_t max_iters;
     int32_t slots;            /* frames resident per CTA; 0 = as many as fit */
+    int32_t threads_per_frame;/* 0: the bp_decode kernel for this N; N/8 (N >= 256): the kernel with
+                                 TMEM-resident groups of 3 stages; N/4 (at least 32): the kernel with
+                                 shared-memory groups of 2 stages; anything else is PC_EUNSUPPORTED */
+    int32_t reserved;         /* 0 */
     int64_t B;                /* frames in this batch */
     const float* d_llr;       /* B x N, 16-byte aligned */
     uint32_t* d_bits;         /* B x ceil(K/32) */

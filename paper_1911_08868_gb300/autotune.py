@@ -1,10 +1,13 @@
-"""Autotuner of the frames resident per CTA ("slots") of the mixed-length launch.
+"""Autotuner of the mixed-length sweep's launch shape per code length: threads per
+frame (which decoder kernel) and frames resident per CTA ("slots").
 
-For each code length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the
-given Eb/N0, the given schedule) with every candidate slot count through a
-single-batch MixedDecoder, times the launches with CUDA events and keeps the
-fastest.  Results are cached per GPU name in a JSON file
-($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
+For each length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the given
+Eb/N0, the given schedule) with every candidate shape through a single-batch
+MixedDecoder, times the launches with CUDA events and keeps the fastest.
+Threads per frame: N/8 (TMEM-resident groups of 3 stages, N >= 256) or
+max(32, N/4) (shared-memory groups of 2 stages).  Results are cached per GPU
+name and library in a JSON file ($PCBP_TUNE_CACHE, default
+~/.cache/pcbp_tune.json).
 """
 from __future__ import annotations
 
@@ -12,7 +15,7 @@ import json
 import os
 from pathlib import Path
 
-CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
+SLOT_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
 
 
 def cache_path() -> Path:
@@ -21,6 +24,13 @@ def cache_path() -> Path:
 
 def crc_for(N: int):
     return (8, 0x9B) if N <= 256 else (24, 0x1B2B117)
+
+
+def threads_candidates(N: int):
+    out = [max(32, N // 4)]
+    if 256 <= N <= 2048:
+        out.append(N // 8)
+    return out
 
 
 def _synthetic(pcbp, inputs, dev, N, K, r, poly, B, ebn0, seed):
@@ -35,9 +45,11 @@ def _synthetic(pcbp, inputs, dev, N, K, r, poly, B, ebn0, seed):
     return code, llr
 
 
-def tune_slots(lengths, sched_for, max_iters: int = 300, frames: int = 16384, ebn0: float = 2.5,
-               device="cuda", use_cache: bool = True, reps: int = 3) -> dict:
-    """Best slot count per length.  sched_for(n) returns the pc_sched for log2 N = n."""
+def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, ebn0: float = 2.5,
+                device="cuda", use_cache: bool = True, reps: int = 3) -> dict:
+    """Fastest {"threads_per_frame": t, "slots": s} per length.  sched_for(n) returns the
+    pc_sched for log2 N = n.  Slot counts above a kernel's limit are clamped by the library,
+    so equal timings are broken toward fewer slots (the smallest count that reaches them)."""
     import torch
 
     from . import inputs, pcbp
@@ -54,27 +66,29 @@ def tune_slots(lengths, sched_for, max_iters: int = 300, frames: int = 16384, eb
     entry = cache.get(key, {})
     best = {}
     for N in lengths:
-        if str(N) in entry:
-            best[N] = int(entry[str(N)])
+        if str(N) in entry and isinstance(entry[str(N)], dict):
+            best[N] = dict(entry[str(N)])
             continue
         K = N // 2
         r, poly = crc_for(N)
         code, llr = _synthetic(pcbp, inputs, dev, N, K, r, poly, frames, ebn0, seed=N)
         sch = sched_for(N.bit_length() - 1)
         times = {}
-        for slots in CANDIDATES:
-            md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots)], dev)
-            md()
-            torch.cuda.synchronize()
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record()
-            for _ in range(reps):
+        for tpf in threads_candidates(N):
+            for slots in SLOT_CANDIDATES:
+                md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots, tpf)], dev)
                 md()
-            t1.record()
-            torch.cuda.synchronize()
-            times[slots] = t0.elapsed_time(t1) / reps
-        best[N] = min(times, key=lambda s: (times[s], -s))
+                torch.cuda.synchronize()
+                t0 = torch.cuda.Event(enable_timing=True)
+                t1 = torch.cuda.Event(enable_timing=True)
+                t0.record()
+                for _ in range(reps):
+                    md()
+                t1.record()
+                torch.cuda.synchronize()
+                times[(tpf, slots)] = t0.elapsed_time(t1) / reps
+        tpf, slots = min(times, key=lambda c: (round(times[c], 3), c[1]))
+        best[N] = {"threads_per_frame": tpf, "slots": slots, "ms": times[(tpf, slots)]}
         entry[str(N)] = best[N]
     if use_cache:
         cache[key] = entry

@@ -455,7 +455,11 @@ int validate_batch(const pc_batch& b)
     if (rc != PC_OK) return rc;
     rc = validate_sched(b.code, &b.sched);
     if (rc != PC_OK) return rc;
-    if (b.max_iters < 0 || b.B < 0 || b.slots < 0) return PC_EINVAL;
+    if (b.max_iters < 0 || b.B < 0 || b.slots < 0 || b.threads_per_frame < 0 || b.reserved != 0) return PC_EINVAL;
+    const int N = b.code->N;
+    const int tpf = b.threads_per_frame;
+    if (tpf != 0 && !(tpf == N / 8 && b.code->n >= 8 && b.code->n <= 11) && !(tpf == std::max(32, N / 4)))
+        return PC_EUNSUPPORTED;
     if (b.B > 0) {
         if (!b.d_llr || !b.d_bits || !b.d_iters || !b.d_crc_ok) return PC_EINVAL;
         if (reinterpret_cast<uintptr_t>(b.d_llr) & 15u) return PC_EINVAL;
@@ -488,7 +492,8 @@ extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void
         fill_params(b.code, b.d_llr, &b.sched, b.max_iters, b.B, b.d_bits, b.d_iters, b.d_crc_ok, &m->P);
         m->n = b.code->n;
         m->fkind = b.sched.fkind;
-        m->tmem = use_tmem_kernel(b.code->n) ? 1 : 0;
+        const int tpf = b.threads_per_frame;
+        m->tmem = (tpf == 0 ? use_tmem_kernel(b.code->n) : (tpf == b.code->N / 8 && b.code->n >= 8)) ? 1 : 0;
         if (b.B > 0) {
             const int rc = m->tmem ? plan_launch3(b.code, b.B, b.sched.fkind, &m->g, b.slots)
                                    : plan_launch2(b.code, b.B, b.sched.fkind, &m->g, b.slots);

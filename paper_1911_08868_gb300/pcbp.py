@@ -53,8 +53,8 @@ class PcEvent(C.Structure):
 
 class PcBatch(C.Structure):
     _fields_ = [("code", C.POINTER(PcCode)), ("sched", PcSched), ("max_iters", C.c_int32), ("slots", C.c_int32),
-                ("B", C.c_int64), ("d_llr", C.c_void_p), ("d_bits", C.c_void_p), ("d_iters", C.c_void_p),
-                ("d_crc_ok", C.c_void_p)]
+                ("threads_per_frame", C.c_int32), ("reserved", C.c_int32), ("B", C.c_int64), ("d_llr", C.c_void_p),
+                ("d_bits", C.c_void_p), ("d_iters", C.c_void_p), ("d_crc_ok", C.c_void_p)]
 
 
 _vp = C.c_void_p
@@ -309,7 +309,8 @@ def bp_decode_mixed(h_table, n_batches, workspace, stream=None):
 class MixedDecoder:
     """Batches of different codes decoded in one persistent sweep (bp_decode_mixed).
 
-    parts: list of (code, sched, max_iters, llr [B, N] CUDA float32 tensor, slots).  Output
+    parts: list of (code, sched, max_iters, llr [B, N] CUDA float32 tensor, slots) or
+    (..., slots, threads_per_frame) (0: the bp_decode kernel for that length).  Output
     tensors per batch are allocated here (`bits[i]`, `iters[i]`, `crc_ok[i]`); the launch
     table is prepared once, so `__call__` only enqueues a memset and one launch per batch (it
     can be captured in a CUDA graph after a first uncaptured call)."""
@@ -321,7 +322,9 @@ class MixedDecoder:
         self.codes = [p[0] for p in parts]          # keep the host structs alive
         self.llr = [p[3] for p in parts]
         self.bits, self.iters, self.crc_ok, self.batches = [], [], [], []
-        for code, sch, max_iters, llr, slots in parts:
+        for part in parts:
+            code, sch, max_iters, llr, slots = part[:5]
+            tpf = part[5] if len(part) > 5 else 0
             B = llr.shape[0]
             bits = torch.empty((B, words_of(code.K)), dtype=torch.int32, device=self.device)
             iters = torch.empty(B, dtype=torch.int32, device=self.device)
@@ -332,7 +335,7 @@ class MixedDecoder:
             b = PcBatch()
             b.code = C.pointer(code)
             b.sched = sch
-            b.max_iters, b.slots, b.B = max_iters, slots, B
+            b.max_iters, b.slots, b.threads_per_frame, b.B = max_iters, slots, tpf, B
             b.d_llr, b.d_bits, b.d_iters, b.d_crc_ok = (llr.data_ptr(), bits.data_ptr(), iters.data_ptr(),
                                                         ok.data_ptr())
             self.batches.append(b)

@@ -169,6 +169,16 @@ def test_mixed_entry_points_validate_on_the_host(pcbp):
     bx.sched = pcbp.sched(fkind=1)
     arr = (pcbp.PcBatch * 1)(bx)
     assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_ECUDA
+    # threads per frame: N/8 (TMEM kernel) and N/4 (shared-memory kernel) only; reserved must be 0
+    for tpf, want in ((48, pcbp.PC_EUNSUPPORTED), (16, pcbp.PC_EUNSUPPORTED), (32, pcbp.PC_ECUDA), (64, pcbp.PC_ECUDA)):
+        bt = pcbp.PcBatch.from_buffer_copy(b)
+        bt.threads_per_frame = tpf
+        arr = (pcbp.PcBatch * 1)(bt)
+        assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == want, tpf
+    br = pcbp.PcBatch.from_buffer_copy(b)
+    br.reserved = 1
+    arr = (pcbp.PcBatch * 1)(br)
+    assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL
     arr = (pcbp.PcBatch * 1)(b)
     assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), 8) == pcbp.PC_ENOMEM
     assert pcbp._lib.bp_mixed_prepare(arr, 65, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_EINVAL

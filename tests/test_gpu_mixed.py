@@ -37,7 +37,7 @@ def per_batch(pcbp, parts):
     import torch
 
     out = []
-    for code, sch, max_iters, llr, _ in parts:
+    for code, sch, max_iters, llr, *_ in parts:
         dec = pcbp.Decoder(code, sch, max_iters, llr.device)
         b, it, ok = dec(llr)
         out.append((b.clone(), it.clone(), ok.clone()))
@@ -118,3 +118,25 @@ def test_mixed_box_plus_and_min_sum_batches(pcbp, oracle):
     for i in range(len(parts)):
         assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1])
         assert torch.equal(ok[i], want[i][2])
+
+
+def test_mixed_threads_per_frame_choices_agree(pcbp, oracle):
+    """Both decoder kernels, chosen per batch by threads per frame, give bp_decode's outputs."""
+    import torch
+
+    dev = gpu_device()
+    sizes = [(2048, 0.5), (1024, 0.5), (512, 0.75), (256, 0.5), (128, 0.5)]
+    parts, _ = make_parts(pcbp, oracle, dev, sizes, 250, seed=13)
+    want = per_batch(pcbp, parts)
+    for wide in (False, True):
+        chosen = []
+        for code, sch, max_iters, llr, slots in parts:
+            N = code.N
+            tpf = max(32, N // 4) if (wide or N < 256) else N // 8
+            chosen.append((code, sch, max_iters, llr, slots, tpf))
+        md = pcbp.MixedDecoder(chosen, dev)
+        bits, iters, ok = md()
+        torch.cuda.synchronize()
+        for i in range(len(parts)):
+            assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1]), (sizes[i], wide)
+            assert torch.equal(ok[i], want[i][2])
