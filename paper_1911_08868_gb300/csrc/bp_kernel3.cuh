@@ -275,7 +275,7 @@ __device__ __forceinline__ void tm_fence(int* v)
 
 // Packs the partition for the sweeps (slot leader, after build_groups).
 template <int LOGN, int KB>
-__device__ __forceinline__ void pack_groups(Ctl3<LOGN, KB>* c)
+__device__ __noinline__ void pack_groups(Ctl3<LOGN, KB>* c)
 {
     constexpr int E = 1 << KB;
     constexpr int TB = LOGN - KB;        // thread-index bits: 5 lane bits, then warp bits
@@ -382,6 +382,78 @@ __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float 
         const float rt = y[e], rb = y[eb];
         y[e] = fnode<FK>(rt, __fadd_rn(lv[eb], rb), alpha);
         y[eb] = __fadd_rn(fnode<FK>(rt, lv[e], alpha), rb);
+    }
+}
+
+// Draws event kev of frame `frame` (Sec. III), records it as the current
+// event (the previous one becomes the event to revert), sets the increment of
+// N_it,reset (Eq. 2) and builds the new partition.  Slot leader only; out of
+// line, so that the iteration loop stays compact.
+template <int LOGN, int KB>
+__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const unsigned char* s_swz, const DevSched& S,
+                                         uint64_t frame, int kev)
+{
+    int level, range;
+    long long blk;
+    signed char order[16];
+    draw_event(S, LOGN, frame, kev, level, range, blk, order);
+    ctl->g.pv_level = ctl->g.ev_level;
+    ctl->g.pv_range = ctl->g.ev_range;
+    ctl->g.pv_blk = ctl->g.ev_blk;
+    ctl->g.have_prev = ctl->g.have_ev;
+    ctl->g.ev_level = level;
+    ctl->g.ev_range = range;
+    ctl->g.ev_blk = blk;
+    ctl->g.have_ev = 1;
+    const long long nz = (1ll << (level + range - 1)) * (long long)(range - 1);
+    long long inc;
+    if (S.mode == 2) {
+        inc = S.it_reset_full;
+    } else {
+        const long long qz = S.D > 0 ? nz / S.D : 0;
+        inc = qz > S.N_min ? qz : S.N_min;
+    }
+    ctl->g.next_inc = int(inc);
+    build_groups<LOGN, KB>(&ctl->g, s_swz, LOGN, true, level, range, blk, order, true);
+    pack_groups<LOGN, KB>(ctl);
+}
+
+// One permuted stage s narrower than a register group (m < KB events), with
+// per-PE addressing: the L sweep (r_sweep false) or the R sweep of stage s.
+// E/2 PEs per thread; out of line (rare).
+template <int LOGN, int E, int T, int FK>
+__device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowmask, int beta, int lo, int m1, int pbit,
+                                          const float* llr_f, float* Lp, float* Rp, uint32_t* xh,
+                                          const unsigned char* s_swz, float alpha)
+{
+    constexpr int n = LOGN;
+    constexpr int N = 1 << LOGN;
+    auto sw = [&](int j) { return swz(s_swz, j); };
+#pragma unroll
+    for (int c = 0; c < E / 2; ++c) {
+        const int q = tid + c * T;
+        int p = n - 1 - s;
+        if (s >= lo && s <= m1 && (q & lowmask) == beta) p = pbit;
+        const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
+        const int b = t | (1 << p);
+        const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
+        const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
+        const float rt = Rp[s * N + sw(t)];
+        const float rb = Rp[s * N + sw(b)];
+        if (!r_sweep) {
+            Lp[s * N + sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
+            Lp[s * N + sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
+        } else {
+            const float o1 = fnode<FK>(rt, __fadd_rn(lb, rb), alpha);
+            const float o2 = __fadd_rn(fnode<FK>(rt, lt, alpha), rb);
+            if (s >= 1) {
+                Rp[(s - 1) * N + sw(t)] = o1;
+                Rp[(s - 1) * N + sw(b)] = o2;
+            } else {
+                if (__fadd_rn(lt, o1) < 0.f) atomicOr(&xh[t >> 5], 1u << (t & 31));
+                if (__fadd_rn(lb, o2) < 0.f) atomicOr(&xh[b >> 5], 1u << (b & 31));
+            }
+        }
     }
 }
 
@@ -494,11 +566,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         float z[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = 0.f;
+        #pragma unroll 1
         for (int gi = 0; gi < ng; ++gi) {
             const int4 rc = ctl->rec[gi];
             const int gl = (rc.x >> 8) & 0xff;
             if ((rc.x >> 16) & 1) continue;
             const uint32_t colR = uint32_t(rc.y + gl * E);
+            #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) tm_st<E>(tm + colR + uint32_t(i * E), z);
             if (gi == 0) {
                 int A[E];
@@ -518,6 +592,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     // first group.
     auto enter_partition = [&](const float* llr_f) {
         const int ng = ctl->g.ng;
+        #pragma unroll 1
         for (int gi = 0; gi < ng; ++gi) {
             const int4 rc = ctl->rec[gi];
             const int s0 = rc.x & 0xff, gl = (rc.x >> 8) & 0xff;
@@ -528,6 +603,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             for (int e = 0; e < E; ++e) A[e] = lp_off + 4 * ((s0 - 1) * N + ph[e]);
             tm_st_i<E>(tm + uint32_t(rc.w), A);
             const uint32_t colR = uint32_t(rc.y + gl * E);
+            #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {     // R level s0+2+i: Rp plane s0+i
                 float v[E];
 #pragma unroll
@@ -557,6 +633,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     // Before a new partition: the interior R messages back to the canonical planes.
     auto leave_partition = [&]() {
         const int ng = ctl->g.ng;
+        #pragma unroll 1
         for (int gi = 0; gi < ng; ++gi) {
             const int4 rc = ctl->rec[gi];
             const int gl = (rc.x >> 8) & 0xff;
@@ -567,6 +644,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             tm_wait_ld();
             tm_fence<E>(A);
             const uint32_t colR = uint32_t(rc.y + gl * E);
+            #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {
                 float v[E];
                 tm_ld<E>(tm + colR + uint32_t(i * E), v);
@@ -639,27 +717,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             tm_wait_st();
 
             // ---------------- L sweep, all groups but the last
+            #pragma unroll 1
             for (int gi = 0; gi < ng - 1; ++gi) {
                 const int4 rc = ctl->rec[gi];
                 const int s0 = rc.x & 0xff, gl = (rc.x >> 8) & 0xff;
                 if ((rc.x >> 16) & 1) {
                     // one permuted stage with per-PE addressing (m < KB events)
-                    const int s = s0;
-                    const int lo = ctl->g.ev_level - 1, m1 = ctl->g.ev_level + ctl->g.ev_range - 2;
-#pragma unroll
-                    for (int c = 0; c < E / 2; ++c) {
-                        const int q = tid + c * T;
-                        int p = n - 1 - s;
-                        if (s >= lo && s <= m1 && (q & lowmask) == beta) p = ctl->g.pbit[s];
-                        const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
-                        const int b = t | (1 << p);
-                        const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
-                        const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
-                        const float rt = Rp[s * N + sw(t)];
-                        const float rb = Rp[s * N + sw(b)];
-                        Lp[s * N + sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
-                        Lp[s * N + sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
-                    }
+                    single_stage<LOGN, E, T, FK>(false, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
+                                                 ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp, Rp,
+                                                 xh, s_swz, alpha);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
@@ -809,35 +875,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             }
 
             // ---------------- R sweep, the other groups in reverse
+            #pragma unroll 1
             for (int gi = ng - 2; gi >= 0; --gi) {
                 const int4 rc = ctl->rec[gi];
                 const int s0 = rc.x & 0xff, gl = (rc.x >> 8) & 0xff;
                 if ((rc.x >> 16) & 1) {
-                    const int s = s0;
-                    if (s > 0 || want_g) {
-                        const int lo = ctl->g.ev_level - 1, m1 = ctl->g.ev_level + ctl->g.ev_range - 2;
-#pragma unroll
-                        for (int c = 0; c < E / 2; ++c) {
-                            const int q = tid + c * T;
-                            int p = n - 1 - s;
-                            if (s >= lo && s <= m1 && (q & lowmask) == beta) p = ctl->g.pbit[s];
-                            const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
-                            const int b = t | (1 << p);
-                            const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
-                            const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
-                            const float rt = Rp[s * N + sw(t)];
-                            const float rb = Rp[s * N + sw(b)];
-                            const float o1 = fnode<FK>(rt, __fadd_rn(lb, rb), alpha);
-                            const float o2 = __fadd_rn(fnode<FK>(rt, lt, alpha), rb);
-                            if (s >= 1) {
-                                Rp[(s - 1) * N + sw(t)] = o1;
-                                Rp[(s - 1) * N + sw(b)] = o2;
-                            } else {
-                                if (__fadd_rn(lt, o1) < 0.f) atomicOr(&xh[t >> 5], 1u << (t & 31));
-                                if (__fadd_rn(lb, o2) < 0.f) atomicOr(&xh[b >> 5], 1u << (b & 31));
-                            }
-                        }
-                    }
+                    if (s0 > 0 || want_g)
+                        single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
+                                                     ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
+                                                     Rp, xh, s_swz, alpha);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
@@ -916,31 +962,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     tm_wait_st();
                     leave_partition();     // interior R of the old partition to the canonical planes
                     sync();
-                    if (tid == 0) {
-                        int level, range;
-                        long long blk;
-                        signed char order[16];
-                        draw_event(S, n, S.frame_base + uint64_t(f), kev, level, range, blk, order);
-                        ctl->g.pv_level = ctl->g.ev_level;
-                        ctl->g.pv_range = ctl->g.ev_range;
-                        ctl->g.pv_blk = ctl->g.ev_blk;
-                        ctl->g.have_prev = ctl->g.have_ev;
-                        ctl->g.ev_level = level;
-                        ctl->g.ev_range = range;
-                        ctl->g.ev_blk = blk;
-                        ctl->g.have_ev = 1;
-                        const long long nz = (1ll << (level + range - 1)) * (long long)(range - 1);
-                        long long inc;
-                        if (S.mode == 2) {
-                            inc = S.it_reset_full;
-                        } else {
-                            const long long qz = S.D > 0 ? nz / S.D : 0;
-                            inc = qz > S.N_min ? qz : S.N_min;
-                        }
-                        ctl->g.next_inc = int(inc);
-                        build_groups<LOGN, KB>(&ctl->g, s_swz, n, true, level, range, blk, order, true);
-                        pack_groups<LOGN, KB>(ctl);
-                    }
+                    if (tid == 0) apply_event<LOGN, KB>(ctl, s_swz, S, S.frame_base + uint64_t(f), kev);
                     fresh = false;
                     sync();
                     // resetVariableNodes: R at the interior levels of the previous
