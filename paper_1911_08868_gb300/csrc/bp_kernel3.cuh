@@ -385,17 +385,135 @@ __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float 
     }
 }
 
-// Draws event kev of frame `frame` (Sec. III), records it as the current
-// event (the previous one becomes the event to revert), sets the increment of
-// N_it,reset (Eq. 2) and builds the new partition.  Slot leader only; out of
-// line, so that the iteration loop stays compact.
+// The partition of build_groups (short_last) plus pack_groups, computed by
+// the 32 lanes of one warp: every lane walks the group list (a few dozen
+// steps), lane 2g + c then builds group g's register bits for class c, and
+// the lane pairs exchange what the packed record needs.  Writes g.ng, g.low,
+// g.beta, g.pbit and the packed records (rec, cmask, swoff) that the TMEM
+// kernel reads; the per-class bit lists of GroupCtl are not kept.
 template <int LOGN, int KB>
-__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const unsigned char* s_swz, const DevSched& S,
-                                         uint64_t frame, int kev)
+__device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsigned char* swt, int level, int range,
+                                                  long long blk, const signed char* order, int lane)
 {
-    int level, range;
-    long long blk;
-    signed char order[16];
+    constexpr int n = LOGN;
+    constexpr int E = 1 << KB;
+    constexpr int TB = LOGN - KB;
+    const int lo = level - 1, hi = level + range - 2, m = hi + 1;
+    if (lane == 0) {
+        c->g.low = n - m;
+        c->g.beta = int(blk);
+    }
+    if (lane < 16) {
+        int pb = n - 1 - lane;
+        if (lane >= lo && lane <= hi) pb = n - level - order[lane - lo];
+        c->g.pbit[lane] = (signed char)pb;
+    }
+    // segments [a, b, kind]: 0 homogeneous, 1 subgraph-local, 2 single stages
+    int seg_a[3], seg_b[3], seg_k[3], nseg = 0;
+    if (m >= KB) {
+        seg_a[nseg] = 0; seg_b[nseg] = hi; seg_k[nseg] = 1; ++nseg;
+        if (hi + 1 <= n - 1) { seg_a[nseg] = hi + 1; seg_b[nseg] = n - 1; seg_k[nseg] = 0; ++nseg; }
+    } else {
+        if (lo >= 1) { seg_a[nseg] = 0; seg_b[nseg] = lo - 1; seg_k[nseg] = 0; ++nseg; }
+        seg_a[nseg] = lo; seg_b[nseg] = hi; seg_k[nseg] = 2; ++nseg;
+        if (hi + 1 <= n - 1) { seg_a[nseg] = hi + 1; seg_b[nseg] = n - 1; seg_k[nseg] = 0; ++nseg; }
+    }
+    // walk the groups: this lane's group gi = lane / 2, its columns before it
+    const int gi = lane >> 1, cls = lane & 1;
+    int ng = 0, my_s0 = 0, my_gl = 0, my_kind = -1, col = 0, acol = G3<LOGN, KB>::ACOL;
+    int my_col = 0, my_acol = 0, last_s0 = 0, last_gl = 0, last_kind = 0;
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int a = seg_a[sg], b = seg_b[sg], kind = seg_k[sg];
+        const int len = b - a + 1;
+        const int first = len % KB == 0 ? KB : len % KB;
+        const bool sl = sg == nseg - 1;
+        int st = a;
+        for (int q = 0; st <= b; ++q) {
+            const int gl = kind == 2 ? 1 : (sl ? (b - st + 1 < KB ? b - st + 1 : KB) : (q == 0 ? first : KB));
+            if (ng == gi) {
+                my_s0 = st; my_gl = gl; my_kind = kind; my_col = col; my_acol = acol;
+            }
+            last_s0 = st; last_gl = gl; last_kind = kind;
+            if (kind != 2) {
+                col += (st == 0 ? 2 * gl - 2 : 2 * gl - 1) * E;   // the last group is corrected below
+                acol += E;
+            }
+            ++ng;
+            st += gl;
+        }
+    }
+    (void)last_s0; (void)last_gl; (void)last_kind;
+    const bool mine = gi < ng;
+    const bool single = my_kind == 2;
+    const bool last = gi == ng - 1;
+    // register bits of (gi, cls)
+    unsigned used = 0, cmask = 0;
+    int contig = -1;
+    if (mine && !single) {
+        signed char P[KB];
+        for (int i = 0; i < my_gl; ++i) {
+            const int stg = my_s0 + i;
+            int bit = n - 1 - stg;
+            if (cls == 1 && my_kind == 1 && stg >= lo && stg <= hi) bit = n - level - order[stg - lo];
+            P[i] = (signed char)bit;
+            used |= 1u << bit;
+        }
+        const int floor_bit = my_kind == 1 ? n - m : 0;
+        int nxt = my_gl;
+        for (int bit = n - 1 - (my_s0 + my_gl); bit >= floor_bit && nxt < KB; --bit)
+            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+        for (int bit = n - my_s0; bit <= n - 1 && nxt < KB; ++bit)
+            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+        for (int bit = floor_bit; bit <= n - 1 && nxt < KB; ++bit)
+            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+        cmask = ((1u << n) - 1u) & ~used;
+        const int lowb = __ffs(used) - 1;
+        contig = (used >> lowb) == ((1u << KB) - 1u) ? lowb : -1;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            int off = 0;
+#pragma unroll
+            for (int i = 0; i < KB; ++i)
+                if ((e >> i) & 1) off |= 1 << P[i];
+            c->swoff[gi][cls][e] = (short)swz(swt, off);
+        }
+    }
+    // warp bits of the thread index in group gi (class 0), ~0 for single or local groups
+    unsigned wb = ~0u;
+    if (mine && !single && my_kind != 1) {
+        unsigned mm = cmask;
+        wb = 0;
+        for (int k = 0; k < TB; ++k) {
+            const unsigned low = mm & (0u - mm);
+            if (k >= 5) wb |= low;
+            mm ^= low;
+        }
+    }
+    const unsigned cmask1 = __shfl_down_sync(0xffffffffu, cmask, 1);
+    const int contig1 = __shfl_down_sync(0xffffffffu, contig, 1);
+    const unsigned wb_next = __shfl_down_sync(0xffffffffu, wb, 2);
+    const unsigned wb_prev = __shfl_up_sync(0xffffffffu, wb, 2);
+    if (mine && cls == 0) {
+        const bool wl_after = !last && wb != ~0u && wb == wb_next;
+        const bool wl_before = gi > 0 && wb != ~0u && wb == wb_prev;
+        // columns of L level s0+1 (virtual for group 0 and the last group), as pack_groups
+        const int colL = last ? my_col - my_gl * E : (my_s0 == 0 ? my_col - E : my_col);
+        c->rec[gi] = make_int4(my_s0 | (my_gl << 8) | (int(single) << 16) | (int(my_kind != 0) << 24) |
+                                   (int(wl_after) << 25) | (int(wl_before) << 26),
+                               colL, (contig & 0xff) | ((contig1 & 0xff) << 8), single ? 0 : my_acol);
+        c->cmask[gi] = make_uint2(cmask, cmask1);
+    }
+    if (lane == 0) c->g.ng = ng;
+}
+
+// Draws event kev of frame `frame` (Sec. III), records it as the current
+// event (the previous one becomes the event to revert) and sets the increment
+// of N_it,reset (Eq. 2).  Slot leader only; out of line, so that the
+// iteration loop stays compact.
+template <int LOGN, int KB>
+__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S, uint64_t frame, int kev, int& level,
+                                         int& range, long long& blk, signed char* order)
+{
     draw_event(S, LOGN, frame, kev, level, range, blk, order);
     ctl->g.pv_level = ctl->g.ev_level;
     ctl->g.pv_range = ctl->g.ev_range;
@@ -414,8 +532,6 @@ __device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const unsigned cha
         inc = qz > S.N_min ? qz : S.N_min;
     }
     ctl->g.next_inc = int(inc);
-    build_groups<LOGN, KB>(&ctl->g, s_swz, LOGN, true, level, range, blk, order, true);
-    pack_groups<LOGN, KB>(ctl);
 }
 
 // One permuted stage s narrower than a register group (m < KB events), with
@@ -962,7 +1078,22 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     tm_wait_st();
                     leave_partition();     // interior R of the old partition to the canonical planes
                     sync();
-                    if (tid == 0) apply_event<LOGN, KB>(ctl, s_swz, S, S.frame_base + uint64_t(f), kev);
+                    if (warp == 0) {
+                        // the slot leader draws the event, the first warp builds the partition
+                        int level = 0, range = 0;
+                        long long blk = 0;
+                        int ord[4] = {0, 0, 0, 0};
+                        if (lane == 0)
+                            apply_event<LOGN, KB>(ctl, S, S.frame_base + uint64_t(f), kev, level, range, blk,
+                                                  reinterpret_cast<signed char*>(ord));
+                        level = __shfl_sync(0xffffffffu, level, 0);
+                        range = __shfl_sync(0xffffffffu, range, 0);
+                        blk = __shfl_sync(0xffffffffu, blk, 0);
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) ord[k] = __shfl_sync(0xffffffffu, ord[k], 0);
+                        build_partition_warp<LOGN, KB>(ctl, s_swz, level, range, blk,
+                                                       reinterpret_cast<const signed char*>(ord), lane);
+                    }
                     fresh = false;
                     sync();
                     // resetVariableNodes: R at the interior levels of the previous
