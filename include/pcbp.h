@@ -189,6 +189,14 @@ int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w
                      const double* d_ckpt, const double* d_glogits, double* d_gw, double* d_gllr,
                      void* d_workspace, void* stream);
 
+/* Self-check of the decoder's internals (no counterpart in the paper): for
+ * every event shape of N = 256..2048 (three orders and blocks each), the
+ * partition the N >= 256 decoder builds with one warp at a switch must equal
+ * the one its single-threaded builder makes.  Writes d_result[0] = shapes
+ * checked, d_result[1] = shapes that differ (device int32[2], 4-byte
+ * aligned), asynchronously on the stream. */
+int pc_partition_selfcheck(int32_t* d_result, void* stream);
+
 /* ---- Mixed-length batched decoding (one persistent sweep) ------------------
  * Several batches, each with its own code (any supported N and rate), schedule
  * and buffers.  Each batch runs the kernel bp_decode runs for its length; the

@@ -65,7 +65,7 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         obj = BUILD / f"bp_inst3_{n}.o"
         jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst3.cu"),
                                                  "-o", str(obj)]))
-    for name in ("bp_decode.cu", "bp_decode_static.cu", "wbp.cu"):
+    for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_selfcheck.cu", "wbp.cu"):
         obj = BUILD / (Path(name).stem + ".o")
         jobs.append((obj, CSRC / name, [*common, "-c", str(CSRC / name), "-o", str(obj)]))
     for name in ("pcbp_host.cpp",):

@@ -506,15 +506,56 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
     if (lane == 0) c->g.ng = ng;
 }
 
-// Draws event kev of frame `frame` (Sec. III), records it as the current
+// draw_event (bp_kernel.cuh) computed by the 32 lanes of a warp: lane d
+// evaluates draw d of the event's counter-based stream, every lane then makes
+// the same choices from those values (fetched with shuffles; draws past 31,
+// needed only after a second identity permutation, are evaluated directly).
+// Same draws and same choices, so the same event.
+__device__ __forceinline__ void draw_event_warp(const DevSched& S, int n, uint64_t frame, int k, int lane, int& level,
+                                                int& range, long long& block, signed char* order)
+{
+    const uint64_t mine = event_draw(S.seed, frame, uint64_t(k), uint64_t(lane));
+    auto draw = [&](int d) -> uint64_t {
+        if (d < 32) {
+            const unsigned lo32 = __shfl_sync(0xffffffffu, unsigned(mine), d);
+            const unsigned hi32 = __shfl_sync(0xffffffffu, unsigned(mine >> 32), d);
+            return (uint64_t(hi32) << 32) | lo32;
+        }
+        return event_draw(S.seed, frame, uint64_t(k), uint64_t(d));
+    };
+    if (S.mode == 2) {
+        range = n;
+        level = 1;
+        block = 0;
+    } else {
+        range = S.rho_fixed > 0 ? S.rho_fixed : 2 + int(draw(0) % uint64_t(S.P_range - 1));
+        const int x = 1 + int(draw(1) % uint64_t(S.P_level));
+        level = min(x, n - range + 1);
+        const int m = level + range - 1;
+        block = (long long)(draw(2) % (1ull << (n - m)));
+    }
+    for (int attempt = 0; attempt < 8; ++attempt) {
+        for (int i = 0; i < range; ++i) order[i] = (signed char)i;
+        for (int i = range - 1; i >= 1; --i) {
+            const int j = int(draw(3 + 16 * attempt + (range - 1 - i)) % uint64_t(i + 1));
+            const signed char t = order[i];
+            order[i] = order[j];
+            order[j] = t;
+        }
+        bool ident = true;
+        for (int i = 0; i < range; ++i) ident = ident && (order[i] == i);
+        if (!ident) return;
+    }
+    for (int i = 0; i < range; ++i) order[i] = (signed char)((i + 1) % range);
+}
+
+// Records event (level, range, blk) of frame `frame` (Sec. III) as the current
 // event (the previous one becomes the event to revert) and sets the increment
 // of N_it,reset (Eq. 2).  Slot leader only; out of line, so that the
 // iteration loop stays compact.
 template <int LOGN, int KB>
-__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S, uint64_t frame, int kev, int& level,
-                                         int& range, long long& blk, signed char* order)
+__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S, int level, int range, long long blk)
 {
-    draw_event(S, LOGN, frame, kev, level, range, blk, order);
     ctl->g.pv_level = ctl->g.ev_level;
     ctl->g.pv_range = ctl->g.ev_range;
     ctl->g.pv_blk = ctl->g.ev_blk;
@@ -1079,20 +1120,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     leave_partition();     // interior R of the old partition to the canonical planes
                     sync();
                     if (warp == 0) {
-                        // the slot leader draws the event, the first warp builds the partition
+                        // the first warp draws the event and builds the partition
                         int level = 0, range = 0;
                         long long blk = 0;
-                        int ord[4] = {0, 0, 0, 0};
-                        if (lane == 0)
-                            apply_event<LOGN, KB>(ctl, S, S.frame_base + uint64_t(f), kev, level, range, blk,
-                                                  reinterpret_cast<signed char*>(ord));
-                        level = __shfl_sync(0xffffffffu, level, 0);
-                        range = __shfl_sync(0xffffffffu, range, 0);
-                        blk = __shfl_sync(0xffffffffu, blk, 0);
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) ord[k] = __shfl_sync(0xffffffffu, ord[k], 0);
-                        build_partition_warp<LOGN, KB>(ctl, s_swz, level, range, blk,
-                                                       reinterpret_cast<const signed char*>(ord), lane);
+                        signed char order[16];
+                        draw_event_warp(S, n, S.frame_base + uint64_t(f), kev, lane, level, range, blk, order);
+                        if (lane == 0) apply_event<LOGN, KB>(ctl, S, level, range, blk);
+                        build_partition_warp<LOGN, KB>(ctl, s_swz, level, range, blk, order, lane);
                     }
                     fresh = false;
                     sync();

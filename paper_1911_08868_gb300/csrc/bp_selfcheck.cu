@@ -1,0 +1,70 @@
+// Internal consistency check of the TMEM kernel's two partition builders
+// (no counterpart in the paper): for every event shape of N = 256..2048 and
+// three orders and blocks each, the warp-parallel builder used at a switch
+// must produce the packed records that build_groups + pack_groups produce.
+#include <cuda_runtime.h>
+
+#include "bp_kernel3.cuh"
+
+namespace pcbp {
+namespace {
+
+template <int LOGN>
+__global__ void partition_selfcheck_kernel(int32_t* result)
+{
+    constexpr int KB = 3, E = 1 << KB;
+    __shared__ Ctl3<LOGN, KB> A, B;
+    __shared__ unsigned char tab[kSwzTableBytes];
+    const int lane = int(threadIdx.x);
+    for (int i = lane; i < kSwzTableBytes; i += 32) tab[i] = swz_row(i);
+    __syncwarp();
+    for (int level = 1; level < LOGN; ++level)
+        for (int range = 2; range <= 16 && level + range - 1 <= LOGN; ++range)
+            for (int v = 0; v < 3; ++v) {
+                const int m = level + range - 1;
+                const long long blk = ((1ll << (LOGN - m)) - 1) * v / 2;      // first, middle, last block
+                signed char order[16];
+                for (int i = 0; i < range; ++i) order[i] = (signed char)(v == 0 ? range - 1 - i : (i + v) % range);
+                if (lane == 0) {
+                    build_groups<LOGN, KB>(&A.g, tab, LOGN, true, level, range, blk, order, true);
+                    pack_groups<LOGN, KB>(&A);
+                }
+                __syncwarp();
+                build_partition_warp<LOGN, KB>(&B, tab, level, range, blk, order, lane);
+                __syncwarp();
+                if (lane == 0) {
+                    int d = (A.g.ng != B.g.ng) + (A.g.low != B.g.low) + (A.g.beta != B.g.beta);
+                    for (int s = 0; s < 16; ++s) d += A.g.pbit[s] != B.g.pbit[s];
+                    for (int g = 0; g < A.g.ng && g < LOGN; ++g) {
+                        const int4 a = A.rec[g], b = B.rec[g];
+                        d += (a.x != b.x) + (a.y != b.y);
+                        if (!((a.x >> 16) & 1)) {             // register groups: bits, offsets, cache column
+                            d += (a.z != b.z) + (a.w != b.w);
+                            d += (A.cmask[g].x != B.cmask[g].x) + (A.cmask[g].y != B.cmask[g].y);
+                            for (int c = 0; c < 2; ++c)
+                                for (int e = 0; e < E; ++e) d += A.swoff[g][c][e] != B.swoff[g][c][e];
+                        }
+                    }
+                    atomicAdd(result + 0, 1);
+                    if (d) atomicAdd(result + 1, 1);
+                }
+                __syncwarp();
+            }
+}
+
+}  // namespace
+}  // namespace pcbp
+
+using namespace pcbp;
+
+extern "C" int pc_partition_selfcheck(int32_t* d_result, void* stream)
+{
+    if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 3u)) return PC_EINVAL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(d_result, 0, 2 * sizeof(int32_t), st) != cudaSuccess) return PC_ECUDA;
+    partition_selfcheck_kernel<8><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<9><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<10><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<11><<<1, 32, 0, st>>>(d_result);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
+}

@@ -21,7 +21,8 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
-            "bp_decode_noalloc", "bp_mixed_table_size", "bp_mixed_prepare", "bp_mixed_workspace_size",
+            "bp_decode_noalloc", "pc_partition_selfcheck", "bp_mixed_table_size", "bp_mixed_prepare",
+            "bp_mixed_workspace_size",
             "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
             "wbp_backward", "wbp_forward_f64", "wbp_backward_f64", "pc_status_string")
 PC_MAX_BATCHES = 64
@@ -67,6 +68,7 @@ _lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c
                                  C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
                                    _vp, _vp]
+_lib.pc_partition_selfcheck.argtypes = [_vp, _vp]
 _lib.bp_mixed_table_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_mixed_prepare.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, C.c_size_t]
 _lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
@@ -281,6 +283,16 @@ class HostDecoder:
             done.append((lo, hi))
         self.compute_stream.synchronize()
         return self.h_bits, self.h_iters, self.h_ok
+
+
+def pc_partition_selfcheck(device="cuda"):
+    """(shapes checked, shapes whose two partition builds differ) of the N >= 256 decoder."""
+    import torch
+
+    out = torch.zeros(2, dtype=torch.int32, device=device)
+    _check("pc_partition_selfcheck", _lib.pc_partition_selfcheck(_ptr(out), _stream(None)))
+    torch.cuda.synchronize()
+    return int(out[0].item()), int(out[1].item())
 
 
 def bp_mixed_table_size(n_batches: int) -> int:

@@ -306,3 +306,11 @@ def test_tmem_and_grouped_kernels_agree(pcbp, oracle, monkeypatch, case):
     assert np.array_equal(ok, gok)
     assert np.array_equal(bits, gbits)
     assert (iters > 2 * kw.get("T0", kw.get("it_reset_full", 1))).any()   # frames that went through switches
+
+
+def test_partition_builders_agree_on_every_event_shape(pcbp):
+    """The warp-parallel partition build used at a switch equals the single-threaded one for every
+    (level, range) of N = 256..2048, three orders and blocks each."""
+    checked, differ = pcbp.pc_partition_selfcheck(gpu_device())
+    assert checked == 3 * sum(1 for n in range(8, 12) for lv in range(1, n) for rg in range(2, 17) if lv + rg - 1 <= n)
+    assert differ == 0
