@@ -130,7 +130,12 @@ int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes);
  *     residue (always 1 when crc_len == 0).
  *   d_workspace: bp_decode_workspace_size bytes, overwritten.
  * Messages are FP32; every FP32 operation is rounded as written (no fused
- * multiply-add), so results are reproducible bit for bit. */
+ * multiply-add), so results are reproducible bit for bit.  N >= 256 runs the
+ * kernel that keeps each stage group's interior messages in tensor memory,
+ * smaller N the shared-memory stage-grouped kernel (the environment variable
+ * PCBP_DECODER=grouped selects the latter for every N; the outputs are the
+ * same).  The frames of a call share a persistent grid: each CTA holds one
+ * frame per slot and fetches the next frame index from d_workspace. */
 int bp_decode(const pc_code* code, const float* d_llr, const pc_sched* sched,
               int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
               uint8_t* d_crc_ok, void* d_workspace, void* stream);

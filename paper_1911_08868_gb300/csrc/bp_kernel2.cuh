@@ -1,5 +1,7 @@
 // Stage-grouped PP-BP decoder kernel for sm_103a (Algorithm 1 of arXiv
-// 1911.08868), the production path of bp_decode.
+// 1911.08868): the bp_decode path for N < 256 (and for every N when
+// PCBP_DECODER=grouped); its stage partition and swizzled planes are also the
+// base of the TMEM kernel (bp_kernel3.cuh).
 //
 // Same arithmetic as bp_kernel.cuh (every FP32 operation explicitly rounded,
 // identical operation order per PE output), organised for fewer barriers and

@@ -1,6 +1,6 @@
-"""One persistent launch over batches of different lengths and rates: the
-results equal bp_decode on each batch alone (and the oracle on sampled
-frames), directly and replayed from a CUDA graph."""
+"""One persistent sweep over batches of different lengths and rates
+(bp_decode_mixed): the results equal bp_decode on each batch alone (and the
+oracle on sampled frames), directly and replayed from a CUDA graph."""
 import numpy as np
 import pytest
 
