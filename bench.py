@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true",
                     help="FER curves over Eb/N0 1.5..4.0 dB instead of the benchmark line")
     ap.add_argument("--sweep-frames", type=int, default=1_000_000)
+    ap.add_argument("--sweep-n", type=int, default=1024, choices=(512, 1024, 2048),
+                    help="code length of the sweep (K = N/2, CRC-24); N != 1024 runs the s=4 T=10 PP-BP, "
+                         "FP-BP and plain BP schedules only")
     ap.add_argument("--sweep-oracle-frames", type=int, default=4096)
     return ap.parse_args()
 
@@ -381,6 +384,14 @@ def run_sweep(args):
 
     dev = torch.device("cuda", 0)
     B, Bo = args.sweep_frames, args.sweep_oracle_frames
+    N, K = args.sweep_n, args.sweep_n // 2          # the sweep's code (the benchmark code by default)
+    n = N.bit_length() - 1
+    schedules = {k: dict(v) for k, v in SWEEP_SCHEDULES.items()}
+    if N != 1024:
+        schedules = {k: v for k, v in schedules.items() if k in ("ppbp_s4_t10", "fpbp_q10_t100", "plain_bp")}
+    for v in schedules.values():
+        if v.get("mode") == 1:
+            v["P_level"] = n - 1
     code = pcbp.pc_construct(N, K, R_CRC, POLY)
     _, fr = O.construct(N, K)
     threads = O.max_threads()
@@ -394,7 +405,7 @@ def run_sweep(args):
         del x
         sub_llr = llr[:Bo].cpu().numpy()
         sub_pay = pay[:Bo].cpu().numpy()
-        for name, kw in SWEEP_SCHEDULES.items():
+        for name, kw in schedules.items():
             max_iters = VARIANT_MAX_ITERS.get(name, MAX_ITERS)
             dec = pcbp.Decoder(code, pcbp.sched(**kw), max_iters, dev)
             t0 = torch.cuda.Event(enable_timing=True)
@@ -422,7 +433,7 @@ def run_sweep(args):
                                  "intervals_overlap": bool(oci[0] <= row["fer_ci95"][1] and row["fer_ci95"][0] <= oci[1])}
             rows.append(row)
         del llr, pay
-    print(json.dumps({"sweep": rows, "code": "N=1024 K=512 CRC-24 (0x1B2B117)", "data": "synthetic BPSK/AWGN",
+    print(json.dumps({"sweep": rows, "code": f"N={N} K={K} CRC-24 (0x1B2B117)", "data": "synthetic BPSK/AWGN",
                       "oracle_cores": threads, "dtype": "f32"}), flush=True)
 
 
