@@ -131,21 +131,22 @@ static __device__ __noinline__ void draw_event(const DevSched& S, int n, uint64_
 template <int FK>
 __device__ __forceinline__ float fnode(float a, float b, float alpha);
 
+// min(|a|,|b|) carrying the sign bit sign(a) XOR sign(b), one instruction
+// (min.xorsign.abs); alpha * that value has exactly the bits of alpha *
+// min(|a|,|b|) with the product sign applied afterwards, for any alpha.
 template <>
 __device__ __forceinline__ float fnode<0>(float a, float b, float alpha)
 {
-    const float m = fminf(fabsf(a), fabsf(b));
-    const float v = __fmul_rn(alpha, m);
-    const uint32_t sg = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
-    return __uint_as_float(__float_as_uint(v) ^ sg);
+    float m;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
+    return __fmul_rn(alpha, m);
 }
 
 template <>
 __device__ __forceinline__ float fnode<1>(float a, float b, float)
 {
-    const float m = fminf(fabsf(a), fabsf(b));
-    const uint32_t sg = (__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u;
-    const float sm = __uint_as_float(__float_as_uint(m) ^ sg);
+    float sm;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(sm) : "f"(a), "f"(b));
     if (isinf(a) || isinf(b)) return sm;
     const float c1 = log1pf(expf(-fabsf(__fadd_rn(a, b))));
     const float c2 = log1pf(expf(-fabsf(__fsub_rn(a, b))));
