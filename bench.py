@@ -11,8 +11,9 @@ LLRs (4.1 GB per step) are resident in HBM and larger than L2.
 
 Prints one JSON line.  `value` is decoded information (payload) Gbit/s over
 all ranks, timed with CUDA events around the decoder launches; `e2e` is the
-same metric through the host-buffer API (pinned host LLRs copied in, results
-copied out, every step).  `--impl reference` times the CPU oracle on a
+same metric through the host-buffer API (bp_decode_host: the decoder reads
+the page-locked host LLRs and writes the results into page-locked host memory
+across the host-device link, every step).  `--impl reference` times the CPU oracle on a
 bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -708,7 +709,9 @@ def run_ours(args):
             line["e2e"] = {"value": world * info_bits * e_steps / el / 1e9, "unit": "Gbit/s",
                            "h2d_bytes_per_step": B * N * 4,
                            "d2h_bytes_per_step": B * (4 * math.ceil(K / 32) + 4 + 1), "steps": e_steps,
-                           "chunks": hdec.chunks, "matches_device_run": same}
+                           "path": "bp_decode_host: the kernel reads the page-locked host LLRs and writes the "
+                                   "results into page-locked host memory across the host-device link",
+                           "matches_device_run": same}
 
     if rank == 0 and not args.no_wbp:
         line["wbp"] = run_wbp(pcbp, inputs, dev, args.steps, args.warmup)

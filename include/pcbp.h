@@ -140,6 +140,26 @@ int bp_decode(const pc_code* code, const float* d_llr, const pc_sched* sched,
               int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
               uint8_t* d_crc_ok, void* d_workspace, void* stream);
 
+/* bp_decode (Algorithm 1) on buffers that stay in host memory: the decoder
+ * reads each frame's LLRs once and writes its results in place across the
+ * host-device link (NVLink-C2C on Grace-Blackwell systems), with no staging
+ * copies.  The paper has no counterpart; the operation is bp_decode's.
+ *   h_llr, h_bits, h_iters, h_crc_ok: laid out as d_llr, d_bits, d_iters,
+ *     d_crc_ok of bp_decode (h_llr 16-byte aligned), each in page-locked
+ *     host memory mapped into the current device's address space
+ *     (cudaHostAlloc / cudaMallocHost, or cudaHostRegister with
+ *     cudaHostRegisterMapped), or in device or managed memory of the current
+ *     device.  The first and the last byte of every buffer must be accessible
+ *     from the device at addresses the buffer's length apart; otherwise
+ *     (pageable memory, a buffer running past its allocation) the call
+ *     returns PC_EINVAL before anything is enqueued.  Caller-owned.
+ *   d_workspace: device memory, bp_decode_workspace_size bytes, overwritten.
+ * Asynchronous on stream: synchronise it before reading the results on the
+ * host.  The outputs equal bp_decode's bit for bit. */
+int bp_decode_host(const pc_code* code, const float* h_llr, const pc_sched* sched,
+                   int32_t max_iters, int64_t B, uint32_t* h_bits, int32_t* h_iters,
+                   uint8_t* h_crc_ok, void* d_workspace, void* stream);
+
 /* bp_decode with every message plane recorded, for verification.
  *   h_events: when not NULL, the k-th switch applies h_events[k] (for every
  *     frame) and no switch follows the n_events-th; n_events <=

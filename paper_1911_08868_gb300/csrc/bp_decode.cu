@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 #include <memory>
@@ -426,6 +427,66 @@ extern "C" int bp_decode(const pc_code* code, const float* d_llr, const pc_sched
                          void* stream)
 {
     return decode_common(code, d_llr, sched, max_iters, B, false, nullptr, 0, nullptr, d_bits, d_iters, d_crc_ok,
+                         d_workspace, stream);
+}
+
+// ---------------------------------------------------------------------------
+// Decoding in place in host memory.
+namespace pcbp {
+namespace {
+
+// Device address of a buffer of `bytes` bytes that the kernels may read and
+// write in place: page-locked host memory mapped into the current device's
+// address space, or device or managed memory of the current device.  The
+// first and the last byte must both be accessible, at device addresses
+// bytes - 1 apart.  Only host-side queries; nothing is enqueued.
+int mapped_address(const void* p, size_t bytes, void** dev)
+{
+    if (!p || bytes == 0) return PC_EINVAL;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+        cudaGetLastError();
+        return PC_ECUDA;
+    }
+    const void* last = static_cast<const char*>(p) + (bytes - 1);
+    cudaPointerAttributes a0, a1;
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess || cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+        cudaGetLastError();
+        return PC_EINVAL;
+    }
+    for (const cudaPointerAttributes* a : {&a0, &a1}) {
+        if (a->type == cudaMemoryTypeUnregistered || !a->devicePointer) return PC_EINVAL;
+        if (a->type == cudaMemoryTypeDevice && a->device != cur) return PC_EINVAL;
+    }
+    if (static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) !=
+        static_cast<ptrdiff_t>(bytes - 1))
+        return PC_EINVAL;
+    *dev = a0.devicePointer;
+    return PC_OK;
+}
+
+}  // namespace
+}  // namespace pcbp
+
+extern "C" int bp_decode_host(const pc_code* code, const float* h_llr, const pc_sched* sched, int32_t max_iters,
+                              int64_t B, uint32_t* h_bits, int32_t* h_iters, uint8_t* h_crc_ok, void* d_workspace,
+                              void* stream)
+{
+    using namespace pcbp;
+    int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    if (B < 0 || max_iters < 0) return PC_EINVAL;
+    if (B == 0) return PC_OK;
+    if (!h_llr || !h_bits || !h_iters || !h_crc_ok || !d_workspace) return PC_EINVAL;
+    const size_t KW = size_t(code->K + 31) / 32;
+    if (uint64_t(B) > uint64_t(SIZE_MAX) / (size_t(code->N) * 4u)) return PC_EINVAL;
+    void *llr = nullptr, *bits = nullptr, *iters = nullptr, *ok = nullptr;
+    if ((rc = mapped_address(h_llr, size_t(B) * size_t(code->N) * 4u, &llr)) != PC_OK) return rc;
+    if ((rc = mapped_address(h_bits, size_t(B) * KW * 4u, &bits)) != PC_OK) return rc;
+    if ((rc = mapped_address(h_iters, size_t(B) * 4u, &iters)) != PC_OK) return rc;
+    if ((rc = mapped_address(h_crc_ok, size_t(B), &ok)) != PC_OK) return rc;
+    return decode_common(code, static_cast<const float*>(llr), sched, max_iters, B, false, nullptr, 0, nullptr,
+                         static_cast<uint32_t*>(bits), static_cast<int32_t*>(iters), static_cast<uint8_t*>(ok),
                          d_workspace, stream);
 }
 

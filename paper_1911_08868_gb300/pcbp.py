@@ -20,7 +20,7 @@ PC_OK, PC_EINVAL, PC_ENOMEM, PC_ECUDA, PC_ETIMEOUT, PC_EUNSUPPORTED = 0, -1, -2,
 PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
-EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_trace",
+EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_host", "bp_decode_trace",
             "bp_decode_noalloc", "pc_partition_selfcheck", "bp_mixed_table_size", "bp_mixed_prepare",
             "bp_mixed_workspace_size",
             "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
@@ -64,6 +64,8 @@ _lib.pc_encode.argtypes = [C.POINTER(PcCode), _vp, _vp, C.c_int64, _vp]
 _lib.bp_decode_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int64, C.POINTER(C.c_size_t)]
 _lib.bp_decode.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp, _vp, _vp,
                            _vp]
+_lib.bp_decode_host.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp, _vp,
+                                _vp, _vp]
 _lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64,
                                  C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
 _lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
@@ -158,6 +160,14 @@ def bp_decode(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_
                                        _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
 
 
+def bp_decode_host(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, workspace, stream=None):
+    """bp_decode on tensors in page-locked host memory (or on the device): the kernel reads and
+    writes them in place.  Asynchronous on the stream."""
+    B = llr.shape[0]
+    _check("bp_decode_host", _lib.bp_decode_host(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
+                                                 _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
+
+
 def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dump, bits, iters, crc_ok, workspace,
                     stream=None):
     """As bp_decode, recording every plane into dump [B, max_iters, 2, n+1, N]; events: list of PcEvent or None."""
@@ -224,64 +234,40 @@ def unpack_bits(words, K: int):
 
 
 class HostDecoder:
-    """Decodes LLRs that live in (pinned) host memory: the batch is cut into
-    chunks whose host-to-device copies run on a copy stream while earlier
-    chunks decode on the compute stream; results are copied back to host
-    buffers.  Device buffers are allocated once per batch shape."""
+    """Decodes LLRs that live in page-locked host memory with one bp_decode_host
+    call: the kernel reads each frame's LLRs across the host-device link and
+    writes bits, iterations and CRC flags into page-locked host tensors, with
+    no staging copies.  Output tensors are allocated once per batch size."""
 
-    def __init__(self, code: PcCode, sch: PcSched, max_iters: int, device="cuda", chunks: int = 8):
+    def __init__(self, code: PcCode, sch: PcSched, max_iters: int, device="cuda"):
         import torch
 
         self.code, self.sched, self.max_iters = code, sch, max_iters
         self.device = torch.device(device)
-        self.chunks = chunks
-        self.copy_stream = torch.cuda.Stream(self.device)
-        self.compute_stream = torch.cuda.Stream(self.device)
-        self.workspace = [torch.empty(bp_decode_workspace_size(code, 1), dtype=torch.uint8, device=self.device)
-                          for _ in range(chunks)]
+        self.stream = torch.cuda.Stream(self.device)
+        self.workspace = torch.empty(bp_decode_workspace_size(code, 1), dtype=torch.uint8, device=self.device)
         self._shape = None
 
     def _ensure(self, B: int):
         import torch
 
         if self._shape != B:
-            N, KW = self.code.N, words_of(self.code.K)
-            self.d_llr = torch.empty((B, N), dtype=torch.float32, device=self.device)
-            self.d_bits = torch.empty((B, KW), dtype=torch.int32, device=self.device)
-            self.d_iters = torch.empty(B, dtype=torch.int32, device=self.device)
-            self.d_ok = torch.empty(B, dtype=torch.uint8, device=self.device)
+            KW = words_of(self.code.K)
             self.h_bits = torch.empty((B, KW), dtype=torch.int32, pin_memory=True)
             self.h_iters = torch.empty(B, dtype=torch.int32, pin_memory=True)
             self.h_ok = torch.empty(B, dtype=torch.uint8, pin_memory=True)
             self._shape = B
 
     def __call__(self, h_llr):
-        """h_llr: pinned float32 [B, N] host tensor -> (bits, iters, crc_ok) host tensors (synchronised)."""
-        import torch
-
-        B = h_llr.shape[0]
-        self._ensure(B)
-        step = (B + self.chunks - 1) // self.chunks
-        done = []
-        for c in range(self.chunks):
-            lo, hi = c * step, min(B, (c + 1) * step)
-            if lo >= hi:
-                break
-            with torch.cuda.stream(self.copy_stream):
-                self.d_llr[lo:hi].copy_(h_llr[lo:hi], non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(self.copy_stream)
-            self.compute_stream.wait_event(ev)
-            with torch.cuda.stream(self.compute_stream):
-                sch = PcSched.from_buffer_copy(self.sched)
-                sch.frame_base = self.sched.frame_base + lo     # chunk frames keep their batch-wide ids
-                bp_decode(self.code, self.d_llr[lo:hi], sch, self.max_iters, self.d_bits[lo:hi],
-                          self.d_iters[lo:hi], self.d_ok[lo:hi], self.workspace[c], self.compute_stream)
-                self.h_bits[lo:hi].copy_(self.d_bits[lo:hi], non_blocking=True)
-                self.h_iters[lo:hi].copy_(self.d_iters[lo:hi], non_blocking=True)
-                self.h_ok[lo:hi].copy_(self.d_ok[lo:hi], non_blocking=True)
-            done.append((lo, hi))
-        self.compute_stream.synchronize()
+        """h_llr: page-locked float32 [B, N] host tensor -> (bits, iters, crc_ok) host tensors (synchronised)."""
+        if h_llr.is_cuda or not h_llr.is_pinned():
+            raise ValueError("h_llr must be a page-locked host tensor (tensor.pin_memory())")
+        if not h_llr.is_contiguous():
+            raise ValueError("h_llr must be contiguous")
+        self._ensure(h_llr.shape[0])
+        bp_decode_host(self.code, h_llr, self.sched, self.max_iters, self.h_bits, self.h_iters, self.h_ok,
+                       self.workspace, self.stream)
+        self.stream.synchronize()
         return self.h_bits, self.h_iters, self.h_ok
 
 

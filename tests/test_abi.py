@@ -112,6 +112,39 @@ def test_bp_decode_validates_before_touching_the_device(pcbp):
     assert _call_decode(pcbp, bad, ok) == pcbp.PC_EINVAL
 
 
+def test_bp_decode_host_validates_before_touching_the_device(pcbp):
+    """Argument errors of the host-buffer entry return PC_EINVAL before any
+    pointer is examined; B == 0 succeeds at once."""
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    s = pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=5)
+    p = lambda v: C.c_void_p(v) if v else None
+
+    def call(B=4, max_iters=10, llr=1, bits=1, iters=1, ok=1, ws=1, sch=s):
+        return pcbp._lib.bp_decode_host(C.byref(code), p(llr * 4096), C.byref(sch), max_iters, B, p(bits * 4096),
+                                        p(iters * 4096), p(ok * 4096), p(ws * 4096), None)
+
+    assert call(B=0) == pcbp.PC_OK
+    assert call(B=-1) == pcbp.PC_EINVAL
+    assert call(max_iters=-1) == pcbp.PC_EINVAL
+    for arg in ("llr", "bits", "iters", "ok", "ws"):
+        assert call(**{arg: 0}) == pcbp.PC_EINVAL
+    bad = pcbp.pc_construct(256, 128, 8, 0x9B)
+    bad.frozen_mask[0] ^= 1
+    assert pcbp._lib.bp_decode_host(C.byref(bad), p(4096), C.byref(s), 10, 4, p(4096), p(4096), p(4096), p(4096),
+                                    None) == pcbp.PC_EINVAL
+
+
+@no_gpu_only
+def test_bp_decode_host_rejects_unmapped_pointers_without_a_device(pcbp):
+    """Placeholder addresses are neither mapped host memory nor device memory:
+    rejected on the host (no device here, so the runtime query itself fails)."""
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    s = pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=5)
+    rc = pcbp._lib.bp_decode_host(C.byref(code), C.c_void_p(4096), C.byref(s), 10, 4, C.c_void_p(4096),
+                                  C.c_void_p(4096), C.c_void_p(4096), C.c_void_p(8192), None)
+    assert rc in (pcbp.PC_EINVAL, pcbp.PC_ECUDA)
+
+
 @no_gpu_only
 def test_trace_validates_events(pcbp):
     code = pcbp.pc_construct(64, 32)
