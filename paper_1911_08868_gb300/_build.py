@@ -61,10 +61,12 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         extra = [f"-DPCBP_KB={int(kb)}"] if kb else []
         jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
+    kb3 = os.environ.get("PCBP_KB3")    # the same override for the tensor-memory kernel
     for n in LOGNS_TMEM:
-        obj = BUILD / f"bp_inst3_{n}.o"
-        jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", "-c", str(CSRC / "bp_inst3.cu"),
-                                                 "-o", str(obj)]))
+        obj = BUILD / (f"bp_inst3_{n}_kb{int(kb3)}.o" if kb3 else f"bp_inst3_{n}.o")
+        extra = [f"-DPCBP_KB3={int(kb3)}"] if kb3 else []
+        jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
+                                                 str(CSRC / "bp_inst3.cu"), "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_selfcheck.cu", "wbp.cu"):
         obj = BUILD / (Path(name).stem + ".o")
         jobs.append((obj, CSRC / name, [*common, "-c", str(CSRC / name), "-o", str(obj)]))

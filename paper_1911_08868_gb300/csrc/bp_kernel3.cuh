@@ -175,8 +175,11 @@ __device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned 
 
 // Largest CTA of the TMEM kernel for a length: 512 threads, or fewer when
 // shared memory or TMEM holds fewer slots (N = 1024: 3 slots of 128 threads).
-template <int LOGN>
-__host__ __device__ constexpr int tmem_max_threads() { return LOGN == 10 ? 384 : (LOGN >= 11 ? 256 : 512); }
+template <int LOGN, int KB>
+__host__ __device__ constexpr int tmem_max_threads()
+{
+    return KB == 3 ? (LOGN == 10 ? 384 : (LOGN >= 11 ? 256 : 512)) : (LOGN >= 11 ? 512 : 768);
+}
 
 // Per-slot control block: the stage partition plus a packed copy that the
 // sweeps read with one 16-byte load per group.
@@ -1187,7 +1190,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 }
 
 template <int LOGN, int KB, int FK>
-__global__ void __launch_bounds__(tmem_max_threads<LOGN>(), 1) bp_decode_tmem_kernel(const __grid_constant__ BpParams P)
+__global__ void __launch_bounds__(tmem_max_threads<LOGN, KB>(), 1) bp_decode_tmem_kernel(const __grid_constant__ BpParams P)
 {
     // a kernel launched after this one may start as soon as SMs free up
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
