@@ -876,11 +876,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             const int beta = ctl->g.beta;
             tm_wait_st();
 
-            // ---------------- L sweep, all groups but the last
-            #pragma unroll 1
-            for (int gi = 0; gi < ng - 1; ++gi) {
+            // ---------------- L sweep, all groups but the last.  Group 0 (stages from 0;
+            // never the last group, a partition has at least n / KB >= 2 groups) takes the
+            // channel LLRs from registers: it runs its own copy of the group step.
+            auto l_group = [&](int gi, auto firstc) {
+                constexpr bool FIRST = decltype(firstc)::value;
                 const int4 rc = ctl->rec[gi];
-                const int s0 = rc.x & 0xff, gl = (rc.x >> 8) & 0xff;
+                const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
                 if ((rc.x >> 16) & 1) {
                     // one permuted stage with per-PE addressing (m < KB events)
                     single_stage<LOGN, E, T, FK>(false, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
@@ -902,14 +904,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         float x[E], rb[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
-                            x[e] = s0 == 0 ? L1[e] : at(A[e], 0);
+                            x[e] = FIRST ? L1[e] : at(A[e], 0);
                             rb[e] = at(A[e], (NPL + GL) * N);                 // R level s0+GL+1 (boundary)
                         }
                         if constexpr (GL > 1) {
 #pragma unroll
                             for (int i = 0; i < GL - 1; ++i) tm_fence<E>(rp[i]);
                         }
-                        if (s0 > 0) tm_st<E>(tm + colL, x);                 // L level s0+1
+                        if constexpr (!FIRST) tm_st<E>(tm + colL, x);       // L level s0+1
 #pragma unroll
                         for (int i = 0; i < GL; ++i) {
                             l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
@@ -924,7 +926,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
                 if (!want_g && ((rc.x >> 25) & 1)) __syncwarp();
                 else sync();
-            }
+            };
+            l_group(0, std::true_type{});
+            #pragma unroll 1
+            for (int gi = 1; gi < ng - 1; ++gi) l_group(gi, std::false_type{});
 
             // ---------------- last group: L sweep, decisions, residue, R sweep
             const int gL = ng - 1;
@@ -1034,13 +1039,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
             }
 
-            // ---------------- R sweep, the other groups in reverse
-            #pragma unroll 1
-            for (int gi = ng - 2; gi >= 0; --gi) {
+            // ---------------- R sweep, the other groups in reverse (group 0 again in its own copy)
+            auto r_group = [&](int gi, auto firstc) {
+                constexpr bool FIRST = decltype(firstc)::value;
                 const int4 rc = ctl->rec[gi];
-                const int s0 = rc.x & 0xff, gl = (rc.x >> 8) & 0xff;
+                const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
                 if ((rc.x >> 16) & 1) {
-                    if (s0 > 0 || want_g)
+                    if (!FIRST || want_g)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                      ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
                                                      Rp, xh, s_swz, alpha);
@@ -1053,7 +1058,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         tm_ld_i<E>(tm + uint32_t(rc.w), A);
 #pragma unroll
                         for (int i = 0; i < GL; ++i)
-                            if (i > 0 || s0 > 0) tm_ld<E>(tm + colL + uint32_t(i * E), lv[i]);   // L level s0+1+i
+                            if (i > 0 || !FIRST) tm_ld<E>(tm + colL + uint32_t(i * E), lv[i]);   // L level s0+1+i
                         tm_wait_ld();
                         tm_fence<E>(A);
                         float y[E];
@@ -1061,18 +1066,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         for (int e = 0; e < E; ++e) y[e] = at(A[e], (NPL + GL) * N);           // R level s0+GL+1
 #pragma unroll
                         for (int i = 0; i < GL; ++i) tm_fence<E>(lv[i]);
-                        if (s0 == 0) {
+                        if constexpr (FIRST) {
 #pragma unroll
                             for (int e = 0; e < E; ++e) lv[0][e] = L1[e];
                         }
 #pragma unroll
                         for (int i = GL - 1; i >= 0; --i) {
-                            const int s = s0 + i;
-                            if (s == 0 && !want_g) continue;
+                            if (FIRST && i == 0 && !want_g) continue;      // stage 0 writes only the G-matrix bits
                             r_layer<E, FK>(y, lv[i], i, alpha);
                             if (i > 0) {
                                 tm_st<E>(tm + colL + uint32_t((GL + i - 1) * E), y);            // R level s0+1+i
-                            } else if (s >= 1) {
+                            } else if (!FIRST) {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
                             } else {
@@ -1090,11 +1094,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
                 // group 0 writes shared state (the G-matrix bits) only for the G-matrix test
                 if (want_g) sync();
-                else if (gi > 0) {
+                else if (!FIRST) {
                     if ((rc.x >> 26) & 1) __syncwarp();
                     else sync();
                 }
-            }
+            };
+            #pragma unroll 1
+            for (int gi = ng - 2; gi >= 1; --gi) r_group(gi, std::false_type{});
+            r_group(0, std::true_type{});
 
             if (want_g) {
                 bool stop = false;
