@@ -940,39 +940,38 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             float pr[E];     // R(n+1): the prior of the last group's positions
             unsigned umask = 0;
             const bool check = S.stop_kind != 0 && it >= S.stop_from;
-            {
-                float rp[KB > 1 ? KB - 1 : 1][E];
-                float xL[KB][E];
+            // the group's stage count as a compile-time constant
+            auto last_body = [&](auto glc) {
+                constexpr int GLL = decltype(glc)::value;
+                float rp[GLL > 1 ? GLL - 1 : 1][E];
+                float xL[GLL][E];
                 float x[E];
                 int cj[E];
                 tm_ld_i<E>(tm + uint32_t(rcL.w), AL);
                 tm_ld<E>(tm + uint32_t(Geo::PCOL), pr);
                 tm_ld_i<E>(tm + uint32_t(Geo::CCOL), cj);
 #pragma unroll
-                for (int i = 0; i < KB - 1; ++i)
-                    if (i < glL - 1) tm_ld<E>(tm + colLL + uint32_t((glL + i) * E), rp[i]);
+                for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tm + colLL + uint32_t((GLL + i) * E), rp[i]);
                 tm_wait_ld();
                 tm_fence<E>(AL);
                 tm_fence<E>(pr);
                 tm_fence<E>(cj);
 #pragma unroll
-                for (int i = 0; i < KB - 1; ++i) tm_fence<E>(rp[i]);
+                for (int i = 0; i < GLL - 1; ++i) tm_fence<E>(rp[i]);
 #pragma unroll
-                for (int e = 0; e < E; ++e) x[e] = s0L == 0 ? L1[e] : at(AL[e], 0);
+                for (int e = 0; e < E; ++e) x[e] = at(AL[e], 0);   // the last group never starts at stage 0
 #pragma unroll
-                for (int i = 0; i < KB; ++i) {
-                    if (i < glL) {
+                for (int i = 0; i < GLL; ++i) {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) xL[i][e] = x[e];
-                        if (i < glL - 1) l_layer<E, FK>(x, rp[i < KB - 1 ? i : 0], i, alpha);
-                        else l_layer<E, FK>(x, pr, i, alpha);
-                    }
+                    for (int e = 0; e < E; ++e) xL[i][e] = x[e];
+                    l_layer<E, FK>(x, i < GLL - 1 ? rp[i < GLL - 1 ? i : 0] : pr, i, alpha);
                 }
-                // a5: decisions u_j = [L(n+1) + R(n+1) < 0] and their CRC residue
+                // a5: decisions u_j = [L(n+1) + R(n+1) < 0], taken as L(n+1) < -R(n+1) (a
+                // rounded sum has the sign of the exact one), and their CRC residue
                 unsigned part = 0;
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
-                    const bool u = __fadd_rn(x[e], pr[e]) < 0.f;
+                    const bool u = x[e] < -pr[e];
                     umask |= u ? 1u << e : 0u;
                     part ^= u ? unsigned(cj[e]) : 0u;
                 }
@@ -994,26 +993,19 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #pragma unroll
                 for (int e = 0; e < E; ++e) y[e] = pr[e];
 #pragma unroll
-                for (int i = KB - 1; i >= 0; --i) {
-                    if (i < glL) {
-                        const int s = s0L + i;               // writes R level s+1
-                        if (s == 0 && !want_g) continue;
-                        r_layer<E, FK>(y, xL[i], i, alpha);
-                        if (i > 0) {
-                            tm_st<E>(tm + colLL + uint32_t((glL + i - 1) * E), y);   // R level s0L+1+i
-                        } else if (s >= 1) {
+                for (int i = GLL - 1; i >= 0; --i) {
+                    r_layer<E, FK>(y, xL[i], i, alpha);
+                    if (i > 0) {
+                        tm_st<E>(tm + colLL + uint32_t((GLL + i - 1) * E), y);   // R level s0L+1+i
+                    } else {
 #pragma unroll
-                            for (int e = 0; e < E; ++e) at(AL[e], NPL * N) = y[e];   // R level s0L+1
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < E; ++e) {
-                                const int j = pos_of(AL[e], s0L);
-                                if (__fadd_rn(L1[e], y[e]) < 0.f) atomicOr(&xh[j >> 5], 1u << (j & 31));
-                            }
-                        }
+                        for (int e = 0; e < E; ++e) at(AL[e], NPL * N) = y[e];   // R level s0L+1
                     }
                 }
-            }
+            };
+            if (glL == KB) last_body(std::integral_constant<int, KB>{});
+            else if (KB > 2 && glL == 2) last_body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
+            else last_body(std::integral_constant<int, 1>{});
             sync();
             const unsigned res = (check && want_crc) ? ctl->crc_part[pb] : 0u;
             // every thread read the residue of iteration it-1 before this barrier; the
