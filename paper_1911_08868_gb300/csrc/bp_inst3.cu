@@ -22,10 +22,10 @@ using Geo = G3<PCBP_LOGN, KB>;
 
 // pdl: programmatic dependent launch, the grid may start while the previous
 // kernel of the stream still runs (for independent batches).
-template <int FK>
+template <int FK, int WG>
 cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st, bool pdl)
 {
-    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK>;
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, WG>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
     if (e != cudaSuccess) return e;
     if (!pdl) {
@@ -48,7 +48,7 @@ cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t 
 template <int FK>
 int occupancy(const LaunchGeom& g)
 {
-    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK>;
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, 0>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) != cudaSuccess)
         return 0;
     int blocks = 0;
@@ -80,7 +80,10 @@ int PCBP_CAT(bp3_occupancy_, PCBP_LOGN)(const LaunchGeom& g, int fkind)
 cudaError_t PCBP_CAT(bp3_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st,
                                              bool pdl)
 {
-    return fkind ? launch_variant<1>(P, g, st, pdl) : launch_variant<0>(P, g, st, pdl);
+    // one kernel per f and per G-matrix test, both fixed for a launch
+    const bool wg = (P.job.S.stop_kind & 2) != 0;
+    if (fkind) return wg ? launch_variant<1, 1>(P, g, st, pdl) : launch_variant<1, 0>(P, g, st, pdl);
+    return wg ? launch_variant<0, 1>(P, g, st, pdl) : launch_variant<0, 0>(P, g, st, pdl);
 }
 
 }  // namespace pcbp

@@ -650,7 +650,7 @@ __device__ __noinline__ void build_template(Ctl3<LOGN, KB>* c, const unsigned ch
     pack_groups<LOGN, KB>(c);
 }
 
-template <int LOGN, int KB, int FK>
+template <int LOGN, int KB, int FK, int WG>
 __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long long* counter, unsigned char* smem,
                                             uint32_t tm_base)
 {
@@ -708,7 +708,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const float alpha = S.alpha;
     const int KW = (K + 31) / 32;
     const int max_iters = J.max_iters;
-    const bool want_g = (S.stop_kind & 2) != 0;
+    constexpr bool want_g = WG != 0;     // the G-matrix test is on (stop_kind & 2), fixed per launch
     const bool want_crc = (S.stop_kind & 1) != 0;
 
     float L1[E];   // channel LLRs of the first group's positions
@@ -1188,7 +1188,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     tm_wait_st();
 }
 
-template <int LOGN, int KB, int FK>
+template <int LOGN, int KB, int FK, int WG>
 __global__ void __launch_bounds__(tmem_max_threads<LOGN, KB>(), 1) bp_decode_tmem_kernel(const __grid_constant__ BpParams P)
 {
     // a kernel launched after this one may start as soon as SMs free up
@@ -1212,7 +1212,7 @@ __global__ void __launch_bounds__(tmem_max_threads<LOGN, KB>(), 1) bp_decode_tme
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm_base = s_tm;
-    if (int(threadIdx.x) < P.slots * G3<LOGN, KB>::T) tmem_frames<LOGN, KB, FK>(P.job, P.counter, smem, tm_base);
+    if (int(threadIdx.x) < P.slots * G3<LOGN, KB>::T) tmem_frames<LOGN, KB, FK, WG>(P.job, P.counter, smem, tm_base);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
