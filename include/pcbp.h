@@ -217,9 +217,12 @@ int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w
 /* Self-check of the decoder's internals (no counterpart in the paper): for
  * every event shape of N = 256..2048 (three orders and blocks each), the
  * partition the N >= 256 decoder builds with one warp at a switch must equal
- * the one its single-threaded builder makes.  Writes d_result[0] = shapes
- * checked, d_result[1] = shapes that differ (device int32[2], 4-byte
- * aligned), asynchronously on the stream. */
+ * the one its single-threaded builder makes, and every partition (the
+ * no-event one included) must have at least two stage groups, every group but
+ * the first and the last being a single stage or a full group.  Writes
+ * d_result[0] = partitions checked, d_result[1] = event shapes whose two
+ * builds differ, d_result[2] = partitions of another shape (device int32[3],
+ * 4-byte aligned), asynchronously on the stream. */
 int pc_partition_selfcheck(int32_t* d_result, void* stream);
 
 /* ---- Mixed-length batched decoding (one persistent sweep) ------------------

@@ -920,9 +920,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #pragma unroll
                         for (int e = 0; e < E; ++e) at(A[e], GL * N) = x[e];          // L level s0+GL+1
                     };
-                    if (gl == KB) body(std::integral_constant<int, KB>{});
-                    else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
-                    else body(std::integral_constant<int, 1>{});
+                    // only group 0 and the last group can have fewer than KB stages: every
+                    // other group is a single stage or a full KB (partition rule of
+                    // build_partition_warp, checked by pc_partition_selfcheck)
+                    if constexpr (FIRST) {
+                        if (gl == KB) body(std::integral_constant<int, KB>{});
+                        else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
+                        else body(std::integral_constant<int, 1>{});
+                    } else {
+                        body(std::integral_constant<int, KB>{});
+                    }
                 }
                 if (!want_g && ((rc.x >> 25) & 1)) __syncwarp();
                 else sync();
@@ -1080,9 +1087,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                             }
                         }
                     };
-                    if (gl == KB) body(std::integral_constant<int, KB>{});
-                    else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
-                    else body(std::integral_constant<int, 1>{});
+                    // only group 0 and the last group can have fewer than KB stages: every
+                    // other group is a single stage or a full KB (partition rule of
+                    // build_partition_warp, checked by pc_partition_selfcheck)
+                    if constexpr (FIRST) {
+                        if (gl == KB) body(std::integral_constant<int, KB>{});
+                        else if (KB > 2 && gl == 2) body(std::integral_constant<int, (KB > 2 ? 2 : 1)>{});
+                        else body(std::integral_constant<int, 1>{});
+                    } else {
+                        body(std::integral_constant<int, KB>{});
+                    }
                 }
                 // group 0 writes shared state (the G-matrix bits) only for the G-matrix test
                 if (want_g) sync();

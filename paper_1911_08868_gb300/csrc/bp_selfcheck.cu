@@ -1,7 +1,10 @@
 // Internal consistency check of the TMEM kernel's two partition builders
 // (no counterpart in the paper): for every event shape of N = 256..2048 and
 // three orders and blocks each, the warp-parallel builder used at a switch
-// must produce the packed records that build_groups + pack_groups produce.
+// must produce the packed records that build_groups + pack_groups produce,
+// and every partition (the no-event one included) must have the shape the
+// kernel's sweeps assume: at least two groups, and every group other than the
+// first and the last either a single stage or a full KB stages.
 #include <cuda_runtime.h>
 
 #include "bp_kernel3.cuh"
@@ -17,6 +20,23 @@ __global__ void partition_selfcheck_kernel(int32_t* result)
     __shared__ unsigned char tab[kSwzTableBytes];
     const int lane = int(threadIdx.x);
     for (int i = lane; i < kSwzTableBytes; i += 32) tab[i] = swz_row(i);
+    __syncwarp();
+    // the group shape the sweeps assume
+    auto irregular = [&](const Ctl3<LOGN, KB>& c) {
+        bool bad = c.g.ng < 2;
+        for (int g = 1; g + 1 < c.g.ng && g < LOGN; ++g) {
+            const int x = c.rec[g].x;
+            bad = bad || (!((x >> 16) & 1) && ((x >> 8) & 0xff) != KB);
+        }
+        return bad;
+    };
+    if (lane == 0) {
+        signed char none[16];
+        build_groups<LOGN, KB>(&A.g, tab, LOGN, false, 0, 0, 0, none, true);
+        pack_groups<LOGN, KB>(&A);
+        atomicAdd(result + 0, 1);
+        if (irregular(A)) atomicAdd(result + 2, 1);
+    }
     __syncwarp();
     for (int level = 1; level < LOGN; ++level)
         for (int range = 2; range <= 16 && level + range - 1 <= LOGN; ++range)
@@ -47,6 +67,7 @@ __global__ void partition_selfcheck_kernel(int32_t* result)
                     }
                     atomicAdd(result + 0, 1);
                     if (d) atomicAdd(result + 1, 1);
+                    if (irregular(A) || irregular(B)) atomicAdd(result + 2, 1);
                 }
                 __syncwarp();
             }
@@ -61,7 +82,7 @@ extern "C" int pc_partition_selfcheck(int32_t* d_result, void* stream)
 {
     if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 3u)) return PC_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(d_result, 0, 2 * sizeof(int32_t), st) != cudaSuccess) return PC_ECUDA;
+    if (cudaMemsetAsync(d_result, 0, 3 * sizeof(int32_t), st) != cudaSuccess) return PC_ECUDA;
     partition_selfcheck_kernel<8><<<1, 32, 0, st>>>(d_result);
     partition_selfcheck_kernel<9><<<1, 32, 0, st>>>(d_result);
     partition_selfcheck_kernel<10><<<1, 32, 0, st>>>(d_result);

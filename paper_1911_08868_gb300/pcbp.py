@@ -272,13 +272,14 @@ class HostDecoder:
 
 
 def pc_partition_selfcheck(device="cuda"):
-    """(shapes checked, shapes whose two partition builds differ) of the N >= 256 decoder."""
+    """(partitions checked, event shapes whose two partition builds differ, partitions whose
+    group shape the sweeps do not assume) of the N >= 256 decoder."""
     import torch
 
-    out = torch.zeros(2, dtype=torch.int32, device=device)
+    out = torch.zeros(3, dtype=torch.int32, device=device)
     _check("pc_partition_selfcheck", _lib.pc_partition_selfcheck(_ptr(out), _stream(None)))
     torch.cuda.synchronize()
-    return int(out[0].item()), int(out[1].item())
+    return int(out[0].item()), int(out[1].item()), int(out[2].item())
 
 
 def bp_mixed_table_size(n_batches: int) -> int:

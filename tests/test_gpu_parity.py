@@ -310,7 +310,11 @@ def test_tmem_and_grouped_kernels_agree(pcbp, oracle, monkeypatch, case):
 
 def test_partition_builders_agree_on_every_event_shape(pcbp):
     """The warp-parallel partition build used at a switch equals the single-threaded one for every
-    (level, range) of N = 256..2048, three orders and blocks each."""
-    checked, differ = pcbp.pc_partition_selfcheck(gpu_device())
-    assert checked == 3 * sum(1 for n in range(8, 12) for lv in range(1, n) for rg in range(2, 17) if lv + rg - 1 <= n)
+    (level, range) of N = 256..2048, three orders and blocks each; every partition, the no-event
+    one included, has the group shape the sweeps assume (at least two groups, each middle group
+    a single stage or a full group)."""
+    checked, differ, irregular = pcbp.pc_partition_selfcheck(gpu_device())
+    shapes = 3 * sum(1 for n in range(8, 12) for lv in range(1, n) for rg in range(2, 17) if lv + rg - 1 <= n)
+    assert checked == shapes + 4            # + the no-event partition of each length
     assert differ == 0
+    assert irregular == 0
