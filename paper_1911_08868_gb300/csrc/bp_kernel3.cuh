@@ -879,11 +879,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             // ---------------- L sweep, all groups but the last.  Group 0 (stages from 0;
             // never the last group, a partition has at least n / KB >= 2 groups) takes the
             // channel LLRs from registers: it runs its own copy of the group step.
-            auto l_group = [&](int gi, auto firstc) {
+            auto l_group = [&](int gi, auto firstc, auto singlesc) {
                 constexpr bool FIRST = decltype(firstc)::value;
+                constexpr bool SINGLES = decltype(singlesc)::value;     // the partition has single stages
                 const int4 rc = ctl->rec[gi];
                 const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
-                if ((rc.x >> 16) & 1) {
+                if (SINGLES && ((rc.x >> 16) & 1)) {
                     // one permuted stage with per-PE addressing (m < KB events)
                     single_stage<LOGN, E, T, FK>(false, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                  ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp, Rp,
@@ -934,9 +935,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 if (!want_g && ((rc.x >> 25) & 1)) __syncwarp();
                 else sync();
             };
-            l_group(0, std::true_type{});
-            #pragma unroll 1
-            for (int gi = 1; gi < ng - 1; ++gi) l_group(gi, std::false_type{});
+            // single stages exist only while the event spans fewer than KB stages
+            const bool singles = ctl->g.have_ev && ctl->g.ev_level + ctl->g.ev_range - 1 < KB;
+            if (!singles) {
+                l_group(0, std::true_type{}, std::false_type{});
+                #pragma unroll 1
+                for (int gi = 1; gi < ng - 1; ++gi) l_group(gi, std::false_type{}, std::false_type{});
+            } else {
+                l_group(0, std::true_type{}, std::true_type{});
+                #pragma unroll 1
+                for (int gi = 1; gi < ng - 1; ++gi) l_group(gi, std::false_type{}, std::true_type{});
+            }
 
             // ---------------- last group: L sweep, decisions, residue, R sweep
             const int gL = ng - 1;
@@ -1039,11 +1048,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             }
 
             // ---------------- R sweep, the other groups in reverse (group 0 again in its own copy)
-            auto r_group = [&](int gi, auto firstc) {
+            auto r_group = [&](int gi, auto firstc, auto singlesc) {
                 constexpr bool FIRST = decltype(firstc)::value;
+                constexpr bool SINGLES = decltype(singlesc)::value;
                 const int4 rc = ctl->rec[gi];
                 const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
-                if ((rc.x >> 16) & 1) {
+                if (SINGLES && ((rc.x >> 16) & 1)) {
                     if (!FIRST || want_g)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                      ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
@@ -1105,9 +1115,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     else sync();
                 }
             };
-            #pragma unroll 1
-            for (int gi = ng - 2; gi >= 1; --gi) r_group(gi, std::false_type{});
-            r_group(0, std::true_type{});
+            if (!singles) {
+                #pragma unroll 1
+                for (int gi = ng - 2; gi >= 1; --gi) r_group(gi, std::false_type{}, std::false_type{});
+                r_group(0, std::true_type{}, std::false_type{});
+            } else {
+                #pragma unroll 1
+                for (int gi = ng - 2; gi >= 1; --gi) r_group(gi, std::false_type{}, std::true_type{});
+                r_group(0, std::true_type{}, std::true_type{});
+            }
 
             if (want_g) {
                 bool stop = false;
