@@ -188,7 +188,9 @@ int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sch
  * information position after T iterations (no CRC, no stop test, no
  * permutation).  Gradients: the minimum takes the gradient (the first
  * operand on ties), an infinite message receives none.
- * FP32 entry points and _f64 twins (for gradient checks). */
+ * FP32 entry points and _f64 twins (for gradient checks).  d_w must be
+ * aligned to two weights (8 bytes for FP32, 16 for FP64): the kernels read a
+ * processing element's (k, k+1) pair in one load; PC_EINVAL otherwise. */
 
 /* Number of weights, T * n * (N/2) * 4. */
 int wbp_weights_count(const pc_code* code, int32_t T, size_t* count);

@@ -68,6 +68,17 @@ __device__ __forceinline__ Real fw(Real a, Real b, Real w)
     return (signbit(a) != signbit(b)) ? -v : v;
 }
 
+// FP32: the signed minimum from one min.xorsign.abs; w times it has exactly the
+// bits of the form above for every w (a product's sign is the XOR of the signs
+// and its magnitude does not depend on them)
+template <>
+__device__ __forceinline__ float fw<float>(float a, float b, float w)
+{
+    float m;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
+    return __fmul_rn(w, m);
+}
+
 __device__ __forceinline__ int ins0(int q, int p) { return ((q >> p) << (p + 1)) | (q & ((1 << p) - 1)); }
 
 __device__ __forceinline__ void bar(unsigned id, unsigned count)
@@ -75,7 +86,21 @@ __device__ __forceinline__ void bar(unsigned id, unsigned count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Two consecutive weights (k, k+1) of one processing element in one load
+// (the weight array is 8-byte aligned for float, 16-byte for double).
+__device__ __forceinline__ float2 ld_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
+__device__ __forceinline__ double2 ld_pair(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
+
+template <typename Real>
+__device__ __forceinline__ Real prior_v(const uint32_t* frozen, int j)
+{
+    return ((frozen[j >> 5] >> (j & 31)) & 1u) ? inf_v<Real>() : Real(0);
+}
+
 // ---------------------------------------------------------------------------
+// Shared memory per frame slot: L at levels 1..n+1, R at levels 2..n+1 (the
+// plane of level n+1 holds the frozen priors, written once per CTA), so every
+// stage reads its R operands from one plane without a per-element test.
 template <typename Real>
 __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_constant__ WbpParams<Real> P)
 {
@@ -90,11 +115,12 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
     __syncthreads();
     const size_t tab = (size_t(NW) * 4 + size_t(K) * 2 + 15) & ~size_t(15);
     const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
-    Real* L = reinterpret_cast<Real*>(smem + tab + size_t(slot) * size_t(2 * n) * N * sizeof(Real));  // levels 1..n+1
-    Real* R = L + size_t(n + 1) * N;                                                                 // levels 2..n
+    Real* L = reinterpret_cast<Real*>(smem + tab + size_t(slot) * size_t(2 * n + 1) * N * sizeof(Real));
+    Real* R = L + (n + 1) * N;                    // plane l-2 = level l, 2 <= l <= n+1
+    for (int j = tid; j < N; j += tps) R[(n - 1) * N + j] = prior_v<Real>(s_frozen, j);
     __shared__ long long s_frame[32];
     const unsigned bid = 1u + unsigned(slot);
-    auto prior = [&](int j) { return ((s_frozen[j >> 5] >> (j & 31)) & 1u) ? inf_v<Real>() : Real(0); };
+    const int wplane = n * NH * 4;                // weights of one iteration
 
     while (true) {
         if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
@@ -107,30 +133,35 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
             for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = Real(0);
         bar(bid, tps);
         for (int it = 0; it < P.T; ++it) {
+            const Real* wt = P.w + size_t(it) * wplane;
             for (int s = 0; s < n; ++s) {
                 const int p = n - 1 - s;
+                const Real* Ls = L + s * N;
+                const Real* Rs = R + s * N;           // level s+2
+                Real* Lo = L + (s + 1) * N;
+                const Real* ws = wt + s * NH * 4;
                 for (int q = tid; q < NH; q += tps) {
                     const int t = ins0(q, p), b = t | (1 << p);
-                    const Real lt = L[s * N + t], lb = L[s * N + b];
-                    const Real rt = s < n - 1 ? R[s * N + t] : prior(t);
-                    const Real rb = s < n - 1 ? R[s * N + b] : prior(b);
-                    const Real* w = P.w + ((size_t(it) * n + s) * NH + q) * 4;
-                    L[(s + 1) * N + t] = fw(lt, radd(lb, rb), w[0]);
-                    L[(s + 1) * N + b] = radd(fw(rt, lt, w[1]), lb);
+                    const Real lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const auto w2 = ld_pair(ws + q * 4);   // k = 0, 1
+                    Lo[t] = fw(lt, radd(lb, rb), w2.x);
+                    Lo[b] = radd(fw(rt, lt, w2.y), lb);
                 }
                 bar(bid, tps);
             }
             if (it == P.T - 1) break;
             for (int s = n - 1; s >= 1; --s) {
                 const int p = n - 1 - s;
+                const Real* Ls = L + s * N;
+                const Real* Rs = R + s * N;           // level s+2
+                Real* Ro = R + (s - 1) * N;           // level s+1
+                const Real* ws = wt + s * NH * 4 + 2;
                 for (int q = tid; q < NH; q += tps) {
                     const int t = ins0(q, p), b = t | (1 << p);
-                    const Real lt = L[s * N + t], lb = L[s * N + b];
-                    const Real rt = s < n - 1 ? R[s * N + t] : prior(t);
-                    const Real rb = s < n - 1 ? R[s * N + b] : prior(b);
-                    const Real* w = P.w + ((size_t(it) * n + s) * NH + q) * 4;
-                    R[(s - 1) * N + t] = fw(rt, radd(lb, rb), w[2]);
-                    R[(s - 1) * N + b] = radd(fw(rt, lt, w[3]), rb);
+                    const Real lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const auto w2 = ld_pair(ws + q * 4);   // k = 2, 3
+                    Ro[t] = fw(rt, radd(lb, rb), w2.x);
+                    Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
                 bar(bid, tps);
             }
@@ -140,12 +171,19 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
                 bar(bid, tps);
             }
         }
-        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[size_t(n) * N + s_info[k]];
+        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[n * N + s_info[k]];
         bar(bid, tps);
     }
 }
 
 // ---------------------------------------------------------------------------
+// Shared memory per frame slot: L at levels 1..n+1, R at levels 2..n+1 (level
+// n+1: the priors, written once per CTA), the gradient of L at levels 1..n+1
+// and two planes for the gradient flowing between R levels.  The R planes hold
+// R before this iteration (copied from the checkpoint in one coalesced pass)
+// for the L sweep, R after it (recomputed in place, as in the forward kernel)
+// for the adjoint of the R sweep, and R before it again (a second copy) for
+// the adjoint of the L sweep.
 template <typename Real>
 __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_constant__ WbpParams<Real> P)
 {
@@ -164,15 +202,15 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
     for (int i = threadIdx.x; i < n * NH * 4; i += blockDim.x) dw[i] = Real(0);
     __syncthreads();
     const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
-    const size_t slot_reals = size_t(3 * n + 3) * N;
+    const size_t slot_reals = size_t(3 * n + 4) * N;
     Real* L = reinterpret_cast<Real*>(smem + tab + dw_bytes) + size_t(slot) * slot_reals;   // levels 1..n+1
-    Real* Rt = L + size_t(n + 1) * N;                                                        // R(it) levels 2..n
-    Real* gL = Rt + size_t(n - 1) * N;                                                       // levels 1..n+1
-    Real* gA = gL + size_t(n + 1) * N;
+    Real* Rt = L + (n + 1) * N;                                                              // R, levels 2..n+1
+    Real* gL = Rt + n * N;                                                                   // levels 1..n+1
+    Real* gA = gL + (n + 1) * N;
     Real* gB = gA + N;
+    for (int j = tid; j < N; j += tps) Rt[(n - 1) * N + j] = prior_v<Real>(s_frozen, j);
     __shared__ long long s_frame[32];
     const unsigned bid = 1u + unsigned(slot);
-    auto prior = [&](int j) { return ((s_frozen[j >> 5] >> (j & 31)) & 1u) ? inf_v<Real>() : Real(0); };
     const Real* wt = P.w + size_t(it) * n * NH * 4;
 
     while (true) {
@@ -181,7 +219,11 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
         const long long f = s_frame[slot];
         if (f >= P.B) break;
         const Real* Rp = P.ckpt + (size_t(it) * P.B + size_t(f)) * (n - 1) * N;   // R(it) before this iteration
-        auto rprev = [&](int s, int j) { return s < n - 1 ? Rp[size_t(s) * N + j] : prior(j); };   // level s+2
+        auto load_rp = [&]() {
+#pragma unroll 4
+            for (int j = tid; j < (n - 1) * N; j += tps) Rt[j] = Rp[j];
+        };
+        load_rp();
         for (int j = tid; j < N; j += tps) L[j] = P.llr[size_t(f) * N + j];
         for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = Real(0);
         for (int j = tid; j < N; j += tps) gA[j] = gB[j] = Real(0);
@@ -189,32 +231,37 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
         // forward recomputation of iteration it
         for (int s = 0; s < n; ++s) {
             const int p = n - 1 - s;
+            const Real* Ls = L + s * N;
+            const Real* Rs = Rt + s * N;                                   // R(it) at level s+2
+            Real* Lo = L + (s + 1) * N;
+            const Real* ws = wt + s * NH * 4;
             for (int q = tid; q < NH; q += tps) {
                 const int t = ins0(q, p), b = t | (1 << p);
-                const Real lt = L[s * N + t], lb = L[s * N + b];
-                const Real rt = rprev(s, t), rb = rprev(s, b);
-                const Real* w = wt + (size_t(s) * NH + q) * 4;
-                L[(s + 1) * N + t] = fw(lt, radd(lb, rb), w[0]);
-                L[(s + 1) * N + b] = radd(fw(rt, lt, w[1]), lb);
+                const Real lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                const auto w2 = ld_pair(ws + q * 4);
+                Lo[t] = fw(lt, radd(lb, rb), w2.x);
+                Lo[b] = radd(fw(rt, lt, w2.y), lb);
             }
             bar(bid, tps);
         }
         if (!last) {
             for (int s = n - 1; s >= 1; --s) {
                 const int p = n - 1 - s;
+                const Real* Ls = L + s * N;
+                const Real* Rs = Rt + s * N;
+                Real* Ro = Rt + (s - 1) * N;
+                const Real* ws = wt + s * NH * 4 + 2;
                 for (int q = tid; q < NH; q += tps) {
                     const int t = ins0(q, p), b = t | (1 << p);
-                    const Real lt = L[s * N + t], lb = L[s * N + b];
-                    const Real rt = s < n - 1 ? Rt[s * N + t] : prior(t);
-                    const Real rb = s < n - 1 ? Rt[s * N + b] : prior(b);
-                    const Real* w = wt + (size_t(s) * NH + q) * 4;
-                    Rt[(s - 1) * N + t] = fw(rt, radd(lb, rb), w[2]);
-                    Rt[(s - 1) * N + b] = radd(fw(rt, lt, w[3]), rb);
+                    const Real lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const auto w2 = ld_pair(ws + q * 4);
+                    Ro[t] = fw(rt, radd(lb, rb), w2.x);
+                    Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
                 bar(bid, tps);
             }
         } else {
-            for (int k = tid; k < K; k += tps) gL[size_t(n) * N + s_info[k]] = P.glogits[size_t(f) * K + k];
+            for (int k = tid; k < K; k += tps) gL[n * N + s_info[k]] = P.glogits[size_t(f) * K + k];
             bar(bid, tps);
         }
         // adjoint of the R sweep: stage s makes R level s+1 from R level s+2 and L level s+1
@@ -222,36 +269,43 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
             const Real* gin = P.gin + size_t(f) * (n - 1) * N;
             for (int s = 1; s <= n - 1; ++s) {
                 const int p = n - 1 - s;
+                const Real* gis = gin + (s - 1) * N;
+                const Real* Rs = Rt + s * N;                                   // R level s+2
+                const Real* Ls = L + s * N;
+                Real* gLs = gL + s * N;
+                const Real* ws = wt + s * NH * 4 + 2;
+                Real* ds = dw + s * NH * 4;
                 for (int q = tid; q < NH; q += tps) {
                     const int t = ins0(q, p), b = t | (1 << p);
-                    const Real gt = radd(gin[size_t(s - 1) * N + t], gA[t]);   // gradient of R level s+1
-                    const Real gb = radd(gin[size_t(s - 1) * N + b], gA[b]);
-                    const Real a = s < n - 1 ? Rt[s * N + t] : prior(t);       // R level s+2
-                    const Real rb = s < n - 1 ? Rt[s * N + b] : prior(b);
-                    const Real lt = L[s * N + t], lb = L[s * N + b];
-                    const Real* w = wt + (size_t(s) * NH + q) * 4;
-                    Real* d = dw + (size_t(s) * NH + q) * 4;
+                    const Real gt = radd(gis[t], gA[t]);                        // gradient of R level s+1
+                    const Real gb = radd(gis[b], gA[b]);
+                    const Real a = Rs[t], rb = Rs[b];
+                    const Real lt = Ls[t], lb = Ls[b];
+                    Real* d = ds + q * 4;
                     Real ct = Real(0), cb = Real(0);
-                    if (gt != Real(0)) {                                        // R_out1 = f(a, lb + rb; w2)
-                        const Real c = radd(lb, rb);
-                        const bool amin = fabs(a) <= fabs(c);
-                        const Real m = amin ? fabs(a) : fabs(c);
-                        atomicAdd(d + 2, rmul(gt, sgn(a) * sgn(c) * m));
-                        if (amin) {
-                            ct = radd(ct, rmul(rmul(gt, w[2]), sgn(c)));
-                        } else {
-                            const Real gc = rmul(rmul(gt, w[2]), sgn(a));
-                            gL[s * N + b] = radd(gL[s * N + b], gc);
-                            cb = radd(cb, gc);
+                    if (gt != Real(0) || gb != Real(0)) {
+                        const auto w2 = ld_pair(ws + q * 4);                    // w[2], w[3]
+                        if (gt != Real(0)) {                                    // R_out1 = f(a, lb + rb; w2)
+                            const Real c = radd(lb, rb);
+                            const bool amin = fabs(a) <= fabs(c);
+                            const Real m = amin ? fabs(a) : fabs(c);
+                            atomicAdd(d + 2, rmul(gt, sgn(a) * sgn(c) * m));
+                            if (amin) {
+                                ct = radd(ct, rmul(rmul(gt, w2.x), sgn(c)));
+                            } else {
+                                const Real gc = rmul(rmul(gt, w2.x), sgn(a));
+                                gLs[b] = radd(gLs[b], gc);
+                                cb = radd(cb, gc);
+                            }
                         }
-                    }
-                    if (gb != Real(0)) {                                        // R_out2 = f(a, lt; w3) + rb
-                        cb = radd(cb, gb);
-                        const bool amin = fabs(a) <= fabs(lt);
-                        const Real m = amin ? fabs(a) : fabs(lt);
-                        atomicAdd(d + 3, rmul(gb, sgn(a) * sgn(lt) * m));
-                        if (amin) ct = radd(ct, rmul(rmul(gb, w[3]), sgn(lt)));
-                        else gL[s * N + t] = radd(gL[s * N + t], rmul(rmul(gb, w[3]), sgn(a)));
+                        if (gb != Real(0)) {                                    // R_out2 = f(a, lt; w3) + rb
+                            cb = radd(cb, gb);
+                            const bool amin = fabs(a) <= fabs(lt);
+                            const Real m = amin ? fabs(a) : fabs(lt);
+                            atomicAdd(d + 3, rmul(gb, sgn(a) * sgn(lt) * m));
+                            if (amin) ct = radd(ct, rmul(rmul(gb, w2.y), sgn(lt)));
+                            else gLs[t] = radd(gLs[t], rmul(rmul(gb, w2.y), sgn(a)));
+                        }
                     }
                     gB[t] = ct;                                                 // contributions to R level s+2
                     gB[b] = cb;
@@ -261,44 +315,57 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
             }
         }
         // adjoint of the L sweep: stage s makes L level s+2 from L level s+1 and R(it) level s+2
+        if (!last) {                  // the R planes hold R(it+1): R(it) again
+            load_rp();
+            bar(bid, tps);
+        }
         Real* gout = P.gout + size_t(f) * (n - 1) * N;
         for (int s = n - 1; s >= 0; --s) {
             const int p = n - 1 - s;
+            const Real* Ls = L + s * N;
+            const Real* Rs = Rt + s * N;
+            Real* gLs = gL + s * N;
+            const Real* gLo = gL + (s + 1) * N;
+            const Real* ws = wt + s * NH * 4;
+            Real* ds = dw + s * NH * 4;
+            Real* gos = gout + size_t(s) * N;
             for (int q = tid; q < NH; q += tps) {
                 const int t = ins0(q, p), b = t | (1 << p);
-                const Real gt = gL[(s + 1) * N + t], gb = gL[(s + 1) * N + b];
-                const Real a = L[s * N + t], lb = L[s * N + b];
-                const Real rt = rprev(s, t), rb = rprev(s, b);
-                const Real* w = wt + (size_t(s) * NH + q) * 4;
-                Real* d = dw + (size_t(s) * NH + q) * 4;
+                const Real gt = gLo[t], gb = gLo[b];
                 Real gRt = Real(0), gRb = Real(0);
-                Real gat = gL[s * N + t], gab = gL[s * N + b];
-                if (gt != Real(0)) {                                            // L_out1 = f(a, lb + rb; w0)
-                    const Real c = radd(lb, rb);
-                    const bool amin = fabs(a) <= fabs(c);
-                    const Real m = amin ? fabs(a) : fabs(c);
-                    atomicAdd(d + 0, rmul(gt, sgn(a) * sgn(c) * m));
-                    if (amin) {
-                        gat = radd(gat, rmul(rmul(gt, w[0]), sgn(c)));
-                    } else {
-                        const Real gc = rmul(rmul(gt, w[0]), sgn(a));
-                        gab = radd(gab, gc);
-                        gRb = radd(gRb, gc);
+                Real gat = gLs[t], gab = gLs[b];
+                if (gt != Real(0) || gb != Real(0)) {
+                    const Real a = Ls[t], lb = Ls[b];
+                    const Real rt = Rs[t], rb = Rs[b];
+                    const auto w2 = ld_pair(ws + q * 4);                        // w[0], w[1]
+                    Real* d = ds + q * 4;
+                    if (gt != Real(0)) {                                        // L_out1 = f(a, lb + rb; w0)
+                        const Real c = radd(lb, rb);
+                        const bool amin = fabs(a) <= fabs(c);
+                        const Real m = amin ? fabs(a) : fabs(c);
+                        atomicAdd(d + 0, rmul(gt, sgn(a) * sgn(c) * m));
+                        if (amin) {
+                            gat = radd(gat, rmul(rmul(gt, w2.x), sgn(c)));
+                        } else {
+                            const Real gc = rmul(rmul(gt, w2.x), sgn(a));
+                            gab = radd(gab, gc);
+                            gRb = radd(gRb, gc);
+                        }
+                    }
+                    if (gb != Real(0)) {                                        // L_out2 = f(rt, a; w1) + lb
+                        gab = radd(gab, gb);
+                        const bool rmin = fabs(rt) <= fabs(a);
+                        const Real m = rmin ? fabs(rt) : fabs(a);
+                        atomicAdd(d + 1, rmul(gb, sgn(rt) * sgn(a) * m));
+                        if (rmin) gRt = radd(gRt, rmul(rmul(gb, w2.y), sgn(a)));
+                        else gat = radd(gat, rmul(rmul(gb, w2.y), sgn(rt)));
                     }
                 }
-                if (gb != Real(0)) {                                            // L_out2 = f(rt, a; w1) + lb
-                    gab = radd(gab, gb);
-                    const bool rmin = fabs(rt) <= fabs(a);
-                    const Real m = rmin ? fabs(rt) : fabs(a);
-                    atomicAdd(d + 1, rmul(gb, sgn(rt) * sgn(a) * m));
-                    if (rmin) gRt = radd(gRt, rmul(rmul(gb, w[1]), sgn(a)));
-                    else gat = radd(gat, rmul(rmul(gb, w[1]), sgn(rt)));
-                }
-                gL[s * N + t] = gat;
-                gL[s * N + b] = gab;
+                gLs[t] = gat;
+                gLs[b] = gab;
                 if (s < n - 1) {
-                    gout[size_t(s) * N + t] = gRt;
-                    gout[size_t(s) * N + b] = gRb;
+                    gos[t] = gRt;
+                    gos[b] = gRb;
                 }
             }
             bar(bid, tps);
@@ -328,7 +395,7 @@ int wbp_geometry(const pc_code* c, int64_t B, size_t real_bytes, bool backward, 
     const int NW = N >= 32 ? N / 32 : 1;
     const size_t tab = (size_t(NW) * 4 + size_t(c->K) * 2 + 15) & ~size_t(15);
     const size_t fixed = tab + (backward ? ((size_t(n) * (N / 2) * 4 * real_bytes + 15) & ~size_t(15)) : 0);
-    const size_t slot = (backward ? size_t(3 * n + 3) : size_t(2 * n)) * N * real_bytes;
+    const size_t slot = (backward ? size_t(3 * n + 4) : size_t(2 * n + 1)) * N * real_bytes;
     g->tps = std::max(32, std::min(512, N / 2));
     if (fixed + slot > size_t(optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(optin) - fixed) / slot);
@@ -360,6 +427,7 @@ int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, in
     if (rc != PC_OK) return rc;
     if (B == 0) return PC_OK;
     if (!llr || !w || !logits || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
+    if (reinterpret_cast<uintptr_t>(w) & (2 * sizeof(Real) - 1)) return PC_EINVAL;   // weights are read in pairs
     Geo g;
     rc = wbp_geometry(c, B, sizeof(Real), false, &g);
     if (rc != PC_OK) return rc;
@@ -391,6 +459,7 @@ int backward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, i
     if (rc != PC_OK) return rc;
     if (B == 0) return PC_OK;
     if (!llr || !w || !ckpt || !glogits || !gw || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
+    if (reinterpret_cast<uintptr_t>(w) & (2 * sizeof(Real) - 1)) return PC_EINVAL;   // weights are read in pairs
     Geo g;
     rc = wbp_geometry(c, B, sizeof(Real), true, &g);
     if (rc != PC_OK) return rc;
