@@ -221,3 +221,22 @@ def test_mixed_entry_points_validate_on_the_host(pcbp):
     assert pcbp._lib.bp_decode_mixed(None, 1, C.c_void_p(4096), None) == pcbp.PC_EINVAL
     zeros = (C.c_char * pcbp.bp_mixed_table_size(1))()
     assert pcbp._lib.bp_decode_mixed(C.cast(zeros, C.c_void_p), 1, C.c_void_p(4096), None) == pcbp.PC_EINVAL
+
+@no_gpu_only
+def test_wbp_entry_points_validate_on_the_host(pcbp):
+    """Argument errors of the weighted-BP calls return PC_EINVAL before anything
+    touches a device: T out of range, NULL buffers, a misaligned workspace, and
+    weights not aligned to a pair (the kernels load a processing element's two
+    weights of a sweep at once)."""
+    code = pcbp.pc_construct(64, 32)
+    p = C.c_void_p
+    fwd, fwd64 = pcbp._lib.wbp_forward, pcbp._lib.wbp_forward_f64
+    bwd = pcbp._lib.wbp_backward
+    assert fwd(C.byref(code), p(4096), p(8192), 0, 4, p(4096), None, p(8192), None) == pcbp.PC_EINVAL
+    assert fwd(C.byref(code), None, p(8192), 2, 4, p(4096), None, p(8192), None) == pcbp.PC_EINVAL
+    assert fwd(C.byref(code), p(4096), p(8192), 2, 4, p(4096), None, p(8192 + 16), None) == pcbp.PC_EINVAL
+    assert fwd(C.byref(code), p(4096), p(8192 + 4), 2, 4, p(4096), None, p(8192), None) == pcbp.PC_EINVAL
+    assert fwd64(C.byref(code), p(4096), p(8192 + 8), 2, 4, p(4096), None, p(8192), None) == pcbp.PC_EINVAL
+    assert bwd(C.byref(code), p(4096), p(8192 + 4), 2, 4, p(4096), p(4096), p(4096), None, p(8192),
+               None) == pcbp.PC_EINVAL
+    assert fwd(C.byref(code), p(4096), p(8192), 2, 0, p(4096), None, p(8192), None) == pcbp.PC_OK
