@@ -263,6 +263,13 @@ int bp_mixed_table_size(int32_t n_batches, size_t* bytes);
  * batch, PC_ENOMEM when bytes is too small; queries the device only after
  * every batch is valid. */
 int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes);
+/* Largest number of frames one CTA of the decoder kernel keeps resident
+ * (pc_batch.slots above it is clamped to it) for this code, threads_per_frame
+ * (as in pc_batch) and f (fkind 0 or 1) on the current device, limited by
+ * shared memory, tensor memory and registers.  No counterpart in the paper; a
+ * host query for autotuners.  PC_EUNSUPPORTED for a threads_per_frame no
+ * kernel has. */
+int bp_slot_limit(const pc_code* code, int32_t threads_per_frame, int32_t fkind, int32_t* max_slots);
 /* Bytes of device workspace of bp_decode_mixed (one frame counter per batch). */
 int bp_mixed_workspace_size(int32_t n_batches, size_t* bytes);
 /* Decodes all batches of a table written by bp_mixed_prepare (PC_EINVAL for

@@ -48,14 +48,15 @@ def _synthetic(pcbp, inputs, dev, N, K, r, poly, B, ebn0, seed):
 def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, ebn0: float = 2.5,
                 device="cuda", use_cache: bool = True, reps: int = 3) -> dict:
     """Fastest {"threads_per_frame": t, "slots": s} per length.  sched_for(n) returns the
-    pc_sched for log2 N = n.  Slot counts above a kernel's limit are clamped by the library,
-    so equal timings are broken toward fewer slots (the smallest count that reaches them)."""
+    pc_sched for log2 N = n.  Candidate slot counts are capped at the kernel's limit on this
+    device (bp_slot_limit), so every reported count is one the launch uses; equal timings are
+    broken toward fewer slots."""
     import torch
 
     from . import inputs, pcbp
 
     dev = torch.device(device)
-    key = f"{torch.cuda.get_device_name(dev)}|{pcbp.library_path()}|{max_iters}|{frames}|{ebn0}"
+    key = f"{torch.cuda.get_device_name(dev)}|{pcbp.library_path()}|{max_iters}|{frames}|{ebn0}|capped"
     cache = {}
     cp = cache_path()
     if use_cache and cp.exists():
@@ -75,7 +76,8 @@ def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, e
         sch = sched_for(N.bit_length() - 1)
         times = {}
         for tpf in threads_candidates(N):
-            for slots in SLOT_CANDIDATES:
+            limit = pcbp.bp_slot_limit(code, tpf, int(sch.fkind))
+            for slots in sorted({min(c, limit) for c in SLOT_CANDIDATES}):
                 md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots, tpf)], dev)
                 md()
                 torch.cuda.synchronize()

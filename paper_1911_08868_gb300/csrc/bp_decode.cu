@@ -567,6 +567,25 @@ extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void
     return PC_OK;
 }
 
+extern "C" int bp_slot_limit(const pc_code* code, int32_t threads_per_frame, int32_t fkind, int32_t* max_slots)
+{
+    using namespace pcbp;
+    if (!code || !max_slots) return PC_EINVAL;
+    int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    if (fkind != 0 && fkind != 1) return PC_EINVAL;
+    const int N = code->N, tpf = threads_per_frame;
+    if (tpf < 0) return PC_EINVAL;
+    if (tpf != 0 && !(tpf == N / 8 && code->n >= 8 && code->n <= 11) && !(tpf == std::max(32, N / 4)))
+        return PC_EUNSUPPORTED;
+    const bool tmem = tpf == 0 ? use_tmem_kernel(code->n) : (tpf == N / 8 && code->n >= 8);
+    LaunchGeom g;
+    rc = tmem ? plan_launch3(code, 1, fkind, &g) : plan_launch2(code, 1, fkind, &g);
+    if (rc != PC_OK) return rc;
+    *max_slots = g.slots;
+    return PC_OK;
+}
+
 extern "C" int bp_mixed_workspace_size(int32_t n_batches, size_t* bytes)
 {
     if (n_batches < 0 || n_batches > PC_MAX_BATCHES || !bytes) return PC_EINVAL;

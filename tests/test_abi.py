@@ -240,3 +240,13 @@ def test_wbp_entry_points_validate_on_the_host(pcbp):
     assert bwd(C.byref(code), p(4096), p(8192 + 4), 2, 4, p(4096), p(4096), p(4096), None, p(8192),
                None) == pcbp.PC_EINVAL
     assert fwd(C.byref(code), p(4096), p(8192), 2, 0, p(4096), None, p(8192), None) == pcbp.PC_OK
+
+
+def test_slot_limit_validates_on_the_host(pcbp):
+    code = pcbp.pc_construct(1024, 512, 24, 0x1B2B117)
+    out = C.c_int32(0)
+    assert pcbp._lib.bp_slot_limit(C.byref(code), 128, 0, None) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_slot_limit(None, 128, 0, C.byref(out)) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_slot_limit(C.byref(code), -1, 0, C.byref(out)) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_slot_limit(C.byref(code), 128, 2, C.byref(out)) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_slot_limit(C.byref(code), 100, 0, C.byref(out)) == pcbp.PC_EUNSUPPORTED

@@ -140,3 +140,28 @@ def test_mixed_threads_per_frame_choices_agree(pcbp, oracle):
         for i in range(len(parts)):
             assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1]), (sizes[i], wide)
             assert torch.equal(ok[i], want[i][2])
+
+
+def test_slot_limit_is_what_a_launch_uses(pcbp, oracle):
+    """bp_slot_limit reports the frames-per-CTA count a batch asking for more is clamped to:
+    a request at the limit and one above it decode alike, for both kernels."""
+    import torch
+
+    dev = gpu_device()
+    sizes = [(1024, 0.5), (256, 0.5), (128, 0.5)]
+    parts, _ = make_parts(pcbp, oracle, dev, sizes, 200, seed=29)
+    for code, sch, max_iters, llr, _ in parts:
+        N = code.N
+        for tpf in sorted({max(32, N // 4)} | ({N // 8} if N >= 256 else set())):
+            lim = pcbp.bp_slot_limit(code, tpf, int(sch.fkind))
+            assert 1 <= lim <= 1024 // tpf
+            outs = []
+            for slots in (lim, lim + 5):
+                md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots, tpf)], dev)
+                outs.append([t[0].clone() for t in md()])
+            torch.cuda.synchronize()
+            for a, b in zip(*outs):
+                assert torch.equal(a, b), (N, tpf)
+    with pytest.raises(pcbp.PcError) as e:
+        pcbp.bp_slot_limit(parts[0][0], 96)
+    assert e.value.status == pcbp.PC_EUNSUPPORTED
