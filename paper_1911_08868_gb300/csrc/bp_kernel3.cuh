@@ -50,6 +50,18 @@
 //
 // One CTA per SM (its shared memory exceeds half an SM's) allocates all 512
 // TMEM columns for its lifetime, so allocations never wait on one another.
+//
+// Compile-time shapes.  Every partition has at least two groups; only the
+// first and the last can have fewer than KB stages, and every group between
+// them is a single stage or a full group (pc_partition_selfcheck checks this
+// for every event shape).  So group 0, whose input is the channel LLRs held in
+// registers, runs its own copy of the group step; the middle groups run the
+// full-group step with no stage-count dispatch, and with no single-stage test
+// unless the current event spans fewer than KB stages; the last group (never
+// starting at stage 0) is dispatched once on its stage count; the G-matrix
+// test is a template parameter.  Each runtime test removed from the loop that
+// every iteration runs took compares, branches, convergence barriers and
+// registers with it.
 #pragma once
 
 #include <type_traits>
