@@ -521,7 +521,7 @@ def run_wbp(pcbp, inputs, dev, steps, warmup):
 
 def run_wbp_train(pcbp, inputs, dev, N=256, T=5, steps=400, lr=2e-3):
     """Trains the per-edge weights (Adam, BCE) on fresh encoder + channel frames every step (batch
-    4096, Eb/N0 uniform on [1, 4] dB), then judges FER on held-out frames against the fixed-scale
+    4096, Eb/N0 uniform on [1, 4] dB), then compares FER on held-out frames with the fixed-scale
     decoder: bp_decode, plain BP, alpha = 0.9375, exactly T iterations (no early stop)."""
     import torch
 
@@ -553,7 +553,7 @@ def run_wbp_train(pcbp, inputs, dev, N=256, T=5, steps=400, lr=2e-3):
         opt.step()
         losses.append(float(loss.item()))
     train_s = time.perf_counter() - t0
-    judge = pcbp.Decoder(code, pcbp.sched(mode=0, stop_kind=0, alpha=0.9375), T, dev)
+    fixed_dec = pcbp.Decoder(code, pcbp.sched(mode=0, stop_kind=0, alpha=0.9375), T, dev)
     test = {}
     for ebn0 in (2.0, 3.0, 4.0):
         errs_w = errs_f = total = 0
@@ -562,7 +562,7 @@ def run_wbp_train(pcbp, inputs, dev, N=256, T=5, steps=400, lr=2e-3):
             with torch.no_grad():
                 logits = pcbp.wbp(llr, w.detach(), code, T)
             got_w = (logits < 0).to(torch.uint8)
-            bits, _, _ = judge(llr)
+            bits, _, _ = fixed_dec(llr)
             got_f = pcbp.unpack_bits(bits, K)
             errs_w += int((got_w != pay).any(dim=1).sum().item())
             errs_f += int((got_f != pay).any(dim=1).sum().item())
