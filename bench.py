@@ -85,7 +85,9 @@ def measured_peaks():
 
 
 def profiled_traffic(sha: str):
-    """DRAM bytes per full launch from the committed ncu summary, if it was taken on this kernel source."""
+    """DRAM bytes per launch of FRAMES frames from the committed ncu summary, if it was taken on this
+    kernel source (the caller scales it to the launch's frame count: the traffic is one LLR read and
+    one result write per frame)."""
     p = ROOT / "profiles" / "bp_decode_tmem_n1024_pp_s4t10.md"
     if not p.exists():
         return None
@@ -662,7 +664,7 @@ def run_ours(args):
     achieved = lane_ops / mean_launch_s
     sha = kernel_sha()
     roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tlane-op/s",
-            "frac": achieved / peak_ops, "traffic": profiled_traffic(sha),
+            "frac": achieved / peak_ops, "traffic": (None if profiled_traffic(sha) is None else profiled_traffic(sha) * B / FRAMES),
             "algorithmic_bytes": B * N * 4 + B * (4 * math.ceil(K / 32) + 5),
             "hbm_gbs": (B * N * 4 + B * (4 * math.ceil(K / 32) + 5)) / mean_launch_s / 1e9,
             "peak_source": ("issue rate 128 lanes/clk/SM x %d SMs x %.0f MHz (MEASURED_PEAKS sm_max_mhz)"
