@@ -265,7 +265,11 @@ class HostDecoder:
             raise ValueError("h_llr must be a page-locked host tensor (tensor.pin_memory())")
         if not h_llr.is_contiguous():
             raise ValueError("h_llr must be contiguous")
+        import torch
+
         self._ensure(h_llr.shape[0])
+        # work the caller queued on its current stream (e.g. an asynchronous fill of h_llr) comes first
+        self.stream.wait_stream(torch.cuda.current_stream(self.device))
         bp_decode_host(self.code, h_llr, self.sched, self.max_iters, self.h_bits, self.h_iters, self.h_ok,
                        self.workspace, self.stream)
         self.stream.synchronize()
