@@ -130,9 +130,10 @@ int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes);
  *     residue (always 1 when crc_len == 0).
  *   d_workspace: bp_decode_workspace_size bytes, overwritten.
  * Messages are FP32; every FP32 operation is rounded as written (no fused
- * multiply-add), so results are reproducible bit for bit.  N >= 256 runs the
- * kernel that keeps each stage group's interior messages in tensor memory,
- * smaller N the shared-memory stage-grouped kernel (the environment variable
+ * multiply-add), so results are reproducible bit for bit.  N >= 128 runs the
+ * kernel that keeps each stage group's interior messages in tensor memory
+ * (groups of 3 stages, of 2 at N = 128), smaller N the shared-memory
+ * stage-grouped kernel (the environment variable
  * PCBP_DECODER=grouped selects the latter for every N; the outputs are the
  * same).  The frames of a call share a persistent grid: each CTA holds one
  * frame per slot and fetches the next frame index from d_workspace. */
@@ -217,8 +218,8 @@ int wbp_backward_f64(const pc_code* code, const double* d_llr, const double* d_w
                      void* d_workspace, void* stream);
 
 /* Self-check of the decoder's internals (no counterpart in the paper): for
- * every event shape of N = 256..2048 (three orders and blocks each), the
- * partition the N >= 256 decoder builds with one warp at a switch must equal
+ * every event shape of N = 128..2048 (three orders and blocks each), the
+ * partition the N >= 128 decoder builds with one warp at a switch must equal
  * the one its single-threaded builder makes, and every partition (the
  * no-event one included) must have at least two stage groups, every group but
  * the first and the last being a single stage or a full group.  Writes
@@ -245,8 +246,10 @@ typedef struct {
     int32_t max_iters;
     int32_t slots;            /* frames resident per CTA; 0 = as many as fit */
     int32_t threads_per_frame;/* 0: the bp_decode kernel for this N; N/8 (N >= 256): the kernel with
-                                 TMEM-resident groups of 3 stages; N/4 (at least 32): the kernel with
-                                 shared-memory groups of 2 stages; anything else is PC_EUNSUPPORTED */
+                                 TMEM-resident groups of 3 stages (groups of 2 at N = 128, where it
+                                 takes 32); N/4 (at least 32): the kernel with shared-memory groups of
+                                 2 stages (at N = 128 only under PCBP_DECODER=grouped, the two
+                                 counts being equal); anything else is PC_EUNSUPPORTED */
     int32_t reserved;         /* 0 */
     int64_t B;                /* frames in this batch */
     const float* d_llr;       /* B x N, 16-byte aligned */

@@ -5,7 +5,8 @@ For each length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the given
 Eb/N0, the given schedule) with every candidate shape through a single-batch
 MixedDecoder, times the launches with CUDA events and keeps the fastest.
 Threads per frame: N/8 (TMEM-resident groups of 3 stages, N >= 256) or
-max(32, N/4) (shared-memory groups of 2 stages).  Results are cached per GPU
+max(32, N/4) (shared-memory groups of 2 stages; at N = 128 the count is 32
+for both kernels and the library runs its TMEM kernel with groups of 2).  Results are cached per GPU
 name and library in a JSON file ($PCBP_TUNE_CACHE, default
 ~/.cache/pcbp_tune.json).
 """

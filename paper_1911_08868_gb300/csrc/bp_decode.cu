@@ -126,6 +126,7 @@ cudaError_t launch2_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cu
 void shape3_of(int n, int* T, size_t* slot, int* max_slots)
 {
     switch (n) {
+        case 7: bp3_shape_7(T, slot, max_slots); break;
         case 8: bp3_shape_8(T, slot, max_slots); break;
         case 9: bp3_shape_9(T, slot, max_slots); break;
         case 10: bp3_shape_10(T, slot, max_slots); break;
@@ -136,6 +137,7 @@ void shape3_of(int n, int* T, size_t* slot, int* max_slots)
 int occupancy3_of(int n, const LaunchGeom& g, int fk)
 {
     switch (n) {
+        case 7: return bp3_occupancy_7(g, fk);
         case 8: return bp3_occupancy_8(g, fk);
         case 9: return bp3_occupancy_9(g, fk);
         case 10: return bp3_occupancy_10(g, fk);
@@ -146,6 +148,7 @@ int occupancy3_of(int n, const LaunchGeom& g, int fk)
 cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st, bool pdl)
 {
     switch (n) {
+        case 7: return bp3_launch_7(P, g, fk, st, pdl);
         case 8: return bp3_launch_8(P, g, fk, st, pdl);
         case 9: return bp3_launch_9(P, g, fk, st, pdl);
         case 10: return bp3_launch_10(P, g, fk, st, pdl);
@@ -156,6 +159,7 @@ cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cu
 void tmem_tables_of(const pc_code* c, size_t* bytes)
 {
     switch (c->n) {
+        case 7: bp3_tables_7(c->N, c->K, bytes); break;
         case 8: bp3_tables_8(c->N, c->K, bytes); break;
         case 9: bp3_tables_9(c->N, c->K, bytes); break;
         case 10: bp3_tables_10(c->N, c->K, bytes); break;
@@ -163,13 +167,32 @@ void tmem_tables_of(const pc_code* c, size_t* bytes)
     }
 }
 
-// The TMEM kernel serves n = 8..11 unless PCBP_DECODER=grouped selects the
-// shared-memory-only kernel (both give identical outputs).
+// The TMEM kernel serves n = 7..11 (groups of 2 stages at n = 7, of 3 from
+// n = 8) unless PCBP_DECODER=grouped selects the shared-memory-only kernel
+// (both give identical outputs).
 bool use_tmem_kernel(int n)
 {
-    if (n < 8 || n > 11) return false;
+    if (n < 7 || n > 11) return false;
     const char* v = std::getenv("PCBP_DECODER");
     return !(v && std::strcmp(v, "grouped") == 0);
+}
+
+// Threads per frame of the TMEM kernel (N / 2^KB), 0 where it has no build.
+int tmem_threads_per_frame(int n)
+{
+    if (n == 7) return (1 << n) / 4;
+    if (n >= 8 && n <= 11) return (1 << n) / 8;
+    return 0;
+}
+
+// The kernel a batch asking for tpf threads per frame runs (tpf valid): at
+// N = 128 both kernels take 32 threads per frame, and the choice follows
+// use_tmem_kernel.
+bool tmem_for(int n, int N, int tpf)
+{
+    if (tpf == 0) return use_tmem_kernel(n);
+    if (tpf != tmem_threads_per_frame(n)) return false;
+    return tpf != std::max(32, N / 4) || use_tmem_kernel(n);
 }
 
 size_t table_bytes(int N, int r, int K)
@@ -519,7 +542,7 @@ int validate_batch(const pc_batch& b)
     if (b.max_iters < 0 || b.B < 0 || b.slots < 0 || b.threads_per_frame < 0 || b.reserved != 0) return PC_EINVAL;
     const int N = b.code->N;
     const int tpf = b.threads_per_frame;
-    if (tpf != 0 && !(tpf == N / 8 && b.code->n >= 8 && b.code->n <= 11) && !(tpf == std::max(32, N / 4)))
+    if (tpf != 0 && tpf != tmem_threads_per_frame(b.code->n) && tpf != std::max(32, N / 4))
         return PC_EUNSUPPORTED;
     if (b.B > 0) {
         if (!b.d_llr || !b.d_bits || !b.d_iters || !b.d_crc_ok) return PC_EINVAL;
@@ -554,7 +577,7 @@ extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void
         m->n = b.code->n;
         m->fkind = b.sched.fkind;
         const int tpf = b.threads_per_frame;
-        m->tmem = (tpf == 0 ? use_tmem_kernel(b.code->n) : (tpf == b.code->N / 8 && b.code->n >= 8)) ? 1 : 0;
+        m->tmem = tmem_for(b.code->n, b.code->N, tpf) ? 1 : 0;
         if (b.B > 0) {
             const int rc = m->tmem ? plan_launch3(b.code, b.B, b.sched.fkind, &m->g, b.slots)
                                    : plan_launch2(b.code, b.B, b.sched.fkind, &m->g, b.slots);
@@ -576,9 +599,9 @@ extern "C" int bp_slot_limit(const pc_code* code, int32_t threads_per_frame, int
     if (fkind != 0 && fkind != 1) return PC_EINVAL;
     const int N = code->N, tpf = threads_per_frame;
     if (tpf < 0) return PC_EINVAL;
-    if (tpf != 0 && !(tpf == N / 8 && code->n >= 8 && code->n <= 11) && !(tpf == std::max(32, N / 4)))
+    if (tpf != 0 && tpf != tmem_threads_per_frame(code->n) && tpf != std::max(32, N / 4))
         return PC_EUNSUPPORTED;
-    const bool tmem = tpf == 0 ? use_tmem_kernel(code->n) : (tpf == N / 8 && code->n >= 8);
+    const bool tmem = tmem_for(code->n, N, tpf);
     LaunchGeom g;
     rc = tmem ? plan_launch3(code, 1, fkind, &g) : plan_launch2(code, 1, fkind, &g);
     if (rc != PC_OK) return rc;

@@ -43,6 +43,7 @@ PCBP_DECLARE_LEN(11)
     int bp3_occupancy_##n(const LaunchGeom& g, int fkind);                                     \
     cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st, bool pdl);
 
+PCBP_DECLARE_LEN3(7)
 PCBP_DECLARE_LEN3(8)
 PCBP_DECLARE_LEN3(9)
 PCBP_DECLARE_LEN3(10)

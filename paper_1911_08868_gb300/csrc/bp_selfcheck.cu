@@ -1,5 +1,5 @@
 // Internal consistency check of the TMEM kernel's two partition builders
-// (no counterpart in the paper): for every event shape of N = 256..2048 and
+// (no counterpart in the paper): for every event shape of N = 128..2048 and
 // three orders and blocks each, the warp-parallel builder used at a switch
 // must produce the packed records that build_groups + pack_groups produce,
 // and every partition (the no-event one included) must have the shape the
@@ -12,10 +12,10 @@
 namespace pcbp {
 namespace {
 
-template <int LOGN>
+template <int LOGN, int KB>
 __global__ void partition_selfcheck_kernel(int32_t* result)
 {
-    constexpr int KB = 3, E = 1 << KB;
+    constexpr int E = 1 << KB;
     __shared__ Ctl3<LOGN, KB> A, B;
     __shared__ unsigned char tab[kSwzTableBytes];
     const int lane = int(threadIdx.x);
@@ -83,9 +83,10 @@ extern "C" int pc_partition_selfcheck(int32_t* d_result, void* stream)
     if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 3u)) return PC_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_result, 0, 3 * sizeof(int32_t), st) != cudaSuccess) return PC_ECUDA;
-    partition_selfcheck_kernel<8><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<9><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<10><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<11><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<7, 2><<<1, 32, 0, st>>>(d_result);     // N = 128: groups of 2 stages
+    partition_selfcheck_kernel<8, 3><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<9, 3><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<10, 3><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<11, 3><<<1, 32, 0, st>>>(d_result);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
 }

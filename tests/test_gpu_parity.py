@@ -278,6 +278,8 @@ def test_full_size_workload_sampled(pcbp, oracle):
 
 # --------------------------------------------------------------------------- the two production kernels
 KERNEL_CASES = [
+    (128, 64, 8, POLY8, 2.0, dict(mode=1, rho_range_fixed=3, P_level=6, N_min=3, T0=3), 60, 3000),
+    (128, 96, 8, POLY8, 2.5, dict(mode=2, it_reset_full=5, q_max=8, stop_kind=3), 50, 1500),
     (256, 128, 8, POLY8, 2.0, dict(mode=1, rho_range_fixed=4, P_level=7, N_min=3, T0=3), 60, 3000),
     (512, 256, 24, POLY24, 1.75, dict(mode=1, P_range=9, P_level=8, D=40, N_min=2, T0=2, stop_kind=3), 80, 1500),
     (1024, 512, 24, POLY24, 2.0, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=4, T0=4), 120, 2000),
@@ -290,8 +292,9 @@ KERNEL_CASES = [
 
 @pytest.mark.parametrize("case", KERNEL_CASES, ids=lambda c: f"N{c[0]}-mode{c[5]['mode']}-f{c[5].get('fkind', 0)}")
 def test_tmem_and_grouped_kernels_agree(pcbp, oracle, monkeypatch, case):
-    """From N = 256 on, bp_decode keeps the interior messages of each stage
-    group in tensor memory; PCBP_DECODER=grouped selects the shared-memory
+    """From N = 128 on, bp_decode keeps the interior messages of each stage
+    group in tensor memory (groups of 2 stages at N = 128, of 3 from 256);
+    PCBP_DECODER=grouped selects the shared-memory
     kernel.  Same arithmetic, so identical outputs, box-plus included (whose
     transcendental functions the CPU oracle does not reproduce bit for bit)."""
     N, K, r, poly, ebn0, kw, max_iters, B = case
@@ -310,11 +313,12 @@ def test_tmem_and_grouped_kernels_agree(pcbp, oracle, monkeypatch, case):
 
 def test_partition_builders_agree_on_every_event_shape(pcbp):
     """The warp-parallel partition build used at a switch equals the single-threaded one for every
-    (level, range) of N = 256..2048, three orders and blocks each; every partition, the no-event
+    (level, range) of N = 128..2048, three orders and blocks each; every partition, the no-event
     one included, has the group shape the sweeps assume (at least two groups, each middle group
     a single stage or a full group)."""
     checked, differ, irregular = pcbp.pc_partition_selfcheck(gpu_device())
     shapes = 3 * sum(1 for n in range(8, 12) for lv in range(1, n) for rg in range(2, 17) if lv + rg - 1 <= n)
-    assert checked == shapes + 4            # + the no-event partition of each length
+    shapes += 3 * sum(1 for lv in range(1, 7) for rg in range(2, 17) if lv + rg - 1 <= 7)   # N = 128
+    assert checked == shapes + 5            # + the no-event partition of each length
     assert differ == 0
     assert irregular == 0
