@@ -132,7 +132,7 @@ int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes);
  * Messages are FP32; every FP32 operation is rounded as written (no fused
  * multiply-add), so results are reproducible bit for bit.  N >= 128 runs the
  * kernel that keeps each stage group's interior messages in tensor memory
- * (groups of 3 stages, of 2 at N = 128), smaller N the shared-memory
+ * (groups of 2 stages up to N = 512, of 3 from 1024), smaller N the shared-memory
  * stage-grouped kernel (the environment variable
  * PCBP_DECODER=grouped selects the latter for every N; the outputs are the
  * same).  The frames of a call share a persistent grid: each CTA holds one
@@ -245,11 +245,11 @@ typedef struct {
     pc_sched sched;           /* frame b draws events with frame id sched.frame_base + b */
     int32_t max_iters;
     int32_t slots;            /* frames resident per CTA; 0 = as many as fit */
-    int32_t threads_per_frame;/* 0: the bp_decode kernel for this N; N/8 (N >= 256): the kernel with
-                                 TMEM-resident groups of 3 stages (groups of 2 at N = 128, where it
-                                 takes 32); N/4 (at least 32): the kernel with shared-memory groups of
-                                 2 stages (at N = 128 only under PCBP_DECODER=grouped, the two
-                                 counts being equal); anything else is PC_EUNSUPPORTED */
+    int32_t threads_per_frame;/* 0: the bp_decode kernel for this N; otherwise the count of one
+                                 kernel as bp_kernel_threads reports it (TMEM-resident stage
+                                 groups: N/4 for N = 128..512, N/8 for 1024 and 2048;
+                                 shared-memory groups: max(32, N/4)); anything else is
+                                 PC_EUNSUPPORTED */
     int32_t reserved;         /* 0 */
     int64_t B;                /* frames in this batch */
     const float* d_llr;       /* B x N, 16-byte aligned */
@@ -266,6 +266,14 @@ int bp_mixed_table_size(int32_t n_batches, size_t* bytes);
  * batch, PC_ENOMEM when bytes is too small; queries the device only after
  * every batch is valid. */
 int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes);
+/* Threads per frame of a decoder kernel for this code (kernel 0: the kernel
+ * with TMEM-resident stage groups, N = 128..2048, groups of 2 stages up to
+ * N = 512 and of 3 from N = 1024, so N/4 or N/8; kernel 1: the shared-memory
+ * stage-grouped kernel, max(32, N/4)), the value pc_batch.threads_per_frame
+ * takes to select it; where the two are equal the TMEM kernel runs unless
+ * PCBP_DECODER=grouped.  Host only, no device call.  No counterpart in the
+ * paper.  PC_EUNSUPPORTED when the kernel has no build for N. */
+int bp_kernel_threads(const pc_code* code, int32_t kernel, int32_t* threads_per_frame);
 /* Largest number of frames one CTA of the decoder kernel keeps resident
  * (pc_batch.slots above it is clamped to it) for this code, threads_per_frame
  * (as in pc_batch) and f (fkind 0 or 1) on the current device, limited by

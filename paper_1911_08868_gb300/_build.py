@@ -26,7 +26,6 @@ LIB = PKG / "libpcbp.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 LOGNS = range(3, 12)
 LOGNS_TMEM = range(7, 12)    # the TMEM kernel needs 2^KB positions on every lane of a warp
-KB3_SMALL = {7: 2}            # N = 128: groups of 2 stages (a warp of 32 threads owns the 128 positions)
 
 
 def _nvcc() -> str:
@@ -64,9 +63,8 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
                                                  str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
     kb3 = os.environ.get("PCBP_KB3")    # the same override for the tensor-memory kernel
     for n in LOGNS_TMEM:
-        k3 = KB3_SMALL.get(n, kb3)
-        obj = BUILD / (f"bp_inst3_{n}_kb{int(k3)}.o" if k3 else f"bp_inst3_{n}.o")
-        extra = [f"-DPCBP_KB3={int(k3)}"] if k3 else []
+        obj = BUILD / (f"bp_inst3_{n}_kb{int(kb3)}.o" if kb3 else f"bp_inst3_{n}.o")
+        extra = [f"-DPCBP_KB3={int(kb3)}"] if kb3 else []
         jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst3.cu"), "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_selfcheck.cu", "wbp.cu"):

@@ -4,9 +4,9 @@ frame (which decoder kernel) and frames resident per CTA ("slots").
 For each length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the given
 Eb/N0, the given schedule) with every candidate shape through a single-batch
 MixedDecoder, times the launches with CUDA events and keeps the fastest.
-Threads per frame: N/8 (TMEM-resident groups of 3 stages, N >= 256) or
-max(32, N/4) (shared-memory groups of 2 stages; at N = 128 the count is 32
-for both kernels and the library runs its TMEM kernel with groups of 2).  Results are cached per GPU
+Threads per frame: the counts bp_kernel_threads reports for the two kernels
+(TMEM-resident stage groups: N/4 up to N = 512, N/8 from 1024; shared-memory
+groups: max(32, N/4); where they coincide the library runs the TMEM kernel).  Results are cached per GPU
 name and library in a JSON file ($PCBP_TUNE_CACHE, default
 ~/.cache/pcbp_tune.json).
 """
@@ -27,11 +27,10 @@ def crc_for(N: int):
     return (8, 0x9B) if N <= 256 else (24, 0x1B2B117)
 
 
-def threads_candidates(N: int):
-    out = [max(32, N // 4)]
-    if 256 <= N <= 2048:
-        out.append(N // 8)
-    return out
+def threads_candidates(pcbp, code):
+    """Distinct threads-per-frame counts that select a decoder kernel for this code (where both
+    kernels take the same count, the library runs the TMEM one)."""
+    return sorted({t for t in (pcbp.bp_kernel_threads(code, k) for k in (0, 1)) if t})
 
 
 def _synthetic(pcbp, inputs, dev, N, K, r, poly, B, ebn0, seed):
@@ -76,7 +75,7 @@ def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, e
         code, llr = _synthetic(pcbp, inputs, dev, N, K, r, poly, frames, ebn0, seed=N)
         sch = sched_for(N.bit_length() - 1)
         times = {}
-        for tpf in threads_candidates(N):
+        for tpf in threads_candidates(pcbp, code):
             limit = pcbp.bp_slot_limit(code, tpf, int(sch.fkind))
             for slots in sorted({min(c, limit) for c in SLOT_CANDIDATES}):
                 md = pcbp.MixedDecoder([(code, sch, max_iters, llr, slots, tpf)], dev)

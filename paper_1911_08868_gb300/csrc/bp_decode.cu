@@ -177,12 +177,14 @@ bool use_tmem_kernel(int n)
     return !(v && std::strcmp(v, "grouped") == 0);
 }
 
-// Threads per frame of the TMEM kernel (N / 2^KB), 0 where it has no build.
+// Threads per frame of the TMEM kernel built for n (N / 2^KB), 0 where it has no build.
 int tmem_threads_per_frame(int n)
 {
-    if (n == 7) return (1 << n) / 4;
-    if (n >= 8 && n <= 11) return (1 << n) / 8;
-    return 0;
+    if (n < 7 || n > 11) return 0;
+    int T = 0, max_slots = 0;
+    size_t slot = 0;
+    shape3_of(n, &T, &slot, &max_slots);
+    return T;
 }
 
 // The kernel a batch asking for tpf threads per frame runs (tpf valid): at
@@ -587,6 +589,18 @@ extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void
         m->magic = kMixedMagic;
         std::memcpy(static_cast<MixedEntry*>(h_table) + i, m.get(), sizeof(MixedEntry));
     }
+    return PC_OK;
+}
+
+extern "C" int bp_kernel_threads(const pc_code* code, int32_t kernel, int32_t* threads_per_frame)
+{
+    using namespace pcbp;
+    if (!code || !threads_per_frame || (kernel != 0 && kernel != 1)) return PC_EINVAL;
+    const int rc = validate_code(code);
+    if (rc != PC_OK) return rc;
+    const int t = kernel == 0 ? tmem_threads_per_frame(code->n) : std::max(32, code->N / 4);
+    if (t == 0) return PC_EUNSUPPORTED;
+    *threads_per_frame = t;
     return PC_OK;
 }
 

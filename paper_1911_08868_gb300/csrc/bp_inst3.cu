@@ -15,7 +15,7 @@ namespace pcbp {
 
 namespace {
 #ifndef PCBP_KB3
-#define PCBP_KB3 3
+#define PCBP_KB3 tmem_default_kb(PCBP_LOGN)
 #endif
 constexpr int KB = PCBP_KB3;   // 2^KB positions per thread
 using Geo = G3<PCBP_LOGN, KB>;

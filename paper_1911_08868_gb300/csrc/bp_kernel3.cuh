@@ -185,6 +185,12 @@ __device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned 
     for (int i = threadIdx.x; i < kSwzTableBytes; i += blockDim.x) s_swz[i] = swz_row(i);
 }
 
+// Stages per group of the TMEM kernel for a length: 2 up to N = 512 (twice the
+// warps per frame, faster there: N = 256 2.15 against 2.84 ms, N = 512 6.87
+// against 7.25 ms on 65,536 PP-BP frames at 2.5 dB), 3 from N = 1024 (N = 1024
+// 8.00 against 9.51 ms, N = 2048 16.9 against 20.4 ms).
+__host__ __device__ constexpr int tmem_default_kb(int logn) { return logn <= 9 ? 2 : 3; }
+
 // Largest CTA of the TMEM kernel for a length: 512 threads, or fewer when
 // shared memory or TMEM holds fewer slots (N = 1024: 3 slots of 128 threads).
 template <int LOGN, int KB>

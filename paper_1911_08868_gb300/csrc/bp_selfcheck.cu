@@ -83,10 +83,11 @@ extern "C" int pc_partition_selfcheck(int32_t* d_result, void* stream)
     if (!d_result || (reinterpret_cast<uintptr_t>(d_result) & 3u)) return PC_EINVAL;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(d_result, 0, 3 * sizeof(int32_t), st) != cudaSuccess) return PC_ECUDA;
-    partition_selfcheck_kernel<7, 2><<<1, 32, 0, st>>>(d_result);     // N = 128: groups of 2 stages
-    partition_selfcheck_kernel<8, 3><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<9, 3><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<10, 3><<<1, 32, 0, st>>>(d_result);
-    partition_selfcheck_kernel<11, 3><<<1, 32, 0, st>>>(d_result);
+    // the group widths the decoder is built with
+    partition_selfcheck_kernel<7, tmem_default_kb(7)><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<8, tmem_default_kb(8)><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<9, tmem_default_kb(9)><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<10, tmem_default_kb(10)><<<1, 32, 0, st>>>(d_result);
+    partition_selfcheck_kernel<11, tmem_default_kb(11)><<<1, 32, 0, st>>>(d_result);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
 }

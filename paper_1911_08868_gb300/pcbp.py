@@ -21,7 +21,8 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_host", "bp_decode_trace",
-            "bp_decode_noalloc", "pc_partition_selfcheck", "bp_slot_limit", "bp_mixed_table_size", "bp_mixed_prepare",
+            "bp_decode_noalloc", "pc_partition_selfcheck", "bp_kernel_threads", "bp_slot_limit", "bp_mixed_table_size",
+            "bp_mixed_prepare",
             "bp_mixed_workspace_size",
             "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
             "wbp_backward", "wbp_forward_f64", "wbp_backward_f64", "pc_status_string")
@@ -76,6 +77,7 @@ _lib.bp_mixed_prepare.argtypes = [C.POINTER(PcBatch), C.c_int32, _vp, C.c_size_t
 _lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_decode_mixed.argtypes = [_vp, C.c_int32, _vp, _vp]
 _lib.bp_slot_limit.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+_lib.bp_kernel_threads.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_int32)]
 _lib.wbp_weights_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_size_t)]
 _lib.wbp_ckpt_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]
 _lib.wbp_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
@@ -285,6 +287,17 @@ def pc_partition_selfcheck(device="cuda"):
     _check("pc_partition_selfcheck", _lib.pc_partition_selfcheck(_ptr(out), _stream(None)))
     torch.cuda.synchronize()
     return int(out[0].item()), int(out[1].item()), int(out[2].item())
+
+
+def bp_kernel_threads(code: PcCode, kernel: int):
+    """Threads per frame that select a decoder kernel (0: TMEM stage groups, 1: shared-memory
+    stage groups) for this code, or None where that kernel has no build for N."""
+    out = C.c_int32(0)
+    rc = _lib.bp_kernel_threads(C.byref(code), kernel, C.byref(out))
+    if rc == PC_EUNSUPPORTED:
+        return None
+    _check("bp_kernel_threads", rc)
+    return out.value
 
 
 def bp_slot_limit(code: PcCode, threads_per_frame: int = 0, fkind: int = 0) -> int:

@@ -202,8 +202,10 @@ def test_mixed_entry_points_validate_on_the_host(pcbp):
     bx.sched = pcbp.sched(fkind=1)
     arr = (pcbp.PcBatch * 1)(bx)
     assert pcbp._lib.bp_mixed_prepare(arr, 1, C.cast(h, C.c_void_p), C.sizeof(h)) == pcbp.PC_ECUDA
-    # threads per frame: N/8 (TMEM kernel) and N/4 (shared-memory kernel) only; reserved must be 0
-    for tpf, want in ((48, pcbp.PC_EUNSUPPORTED), (16, pcbp.PC_EUNSUPPORTED), (32, pcbp.PC_ECUDA), (64, pcbp.PC_ECUDA)):
+    # threads per frame: the counts bp_kernel_threads reports (at N = 256 both kernels take N/4 = 64)
+    # only; reserved must be 0
+    for tpf, want in ((48, pcbp.PC_EUNSUPPORTED), (16, pcbp.PC_EUNSUPPORTED), (32, pcbp.PC_EUNSUPPORTED),
+                      (64, pcbp.PC_ECUDA)):
         bt = pcbp.PcBatch.from_buffer_copy(b)
         bt.threads_per_frame = tpf
         arr = (pcbp.PcBatch * 1)(bt)
@@ -250,3 +252,18 @@ def test_slot_limit_validates_on_the_host(pcbp):
     assert pcbp._lib.bp_slot_limit(C.byref(code), -1, 0, C.byref(out)) == pcbp.PC_EINVAL
     assert pcbp._lib.bp_slot_limit(C.byref(code), 128, 2, C.byref(out)) == pcbp.PC_EINVAL
     assert pcbp._lib.bp_slot_limit(C.byref(code), 100, 0, C.byref(out)) == pcbp.PC_EUNSUPPORTED
+
+
+def test_kernel_threads_is_a_host_query(pcbp):
+    """Threads per frame of each decoder kernel, without a device: the TMEM kernel takes N/4 up
+    to N = 512 and N/8 from 1024 and has no build below N = 128; the shared-memory kernel takes
+    max(32, N/4)."""
+    want = {64: (None, 32), 128: (32, 32), 256: (64, 64), 512: (128, 128), 1024: (128, 256), 2048: (256, 512)}
+    for N, (t0, t1) in want.items():
+        code = pcbp.pc_construct(N, N // 2)
+        assert pcbp.bp_kernel_threads(code, 0) == t0, N
+        assert pcbp.bp_kernel_threads(code, 1) == t1, N
+    out = C.c_int32(0)
+    code = pcbp.pc_construct(256, 128)
+    assert pcbp._lib.bp_kernel_threads(C.byref(code), 2, C.byref(out)) == pcbp.PC_EINVAL
+    assert pcbp._lib.bp_kernel_threads(C.byref(code), 0, None) == pcbp.PC_EINVAL

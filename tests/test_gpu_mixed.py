@@ -120,25 +120,27 @@ def test_mixed_box_plus_and_min_sum_batches(pcbp, oracle):
         assert torch.equal(ok[i], want[i][2])
 
 
-def test_mixed_threads_per_frame_choices_agree(pcbp, oracle):
-    """Both decoder kernels, chosen per batch by threads per frame, give bp_decode's outputs."""
+def test_mixed_threads_per_frame_choices_agree(pcbp, oracle, monkeypatch):
+    """Both decoder kernels, chosen per batch by threads per frame (bp_kernel_threads; where the
+    two counts coincide PCBP_DECODER=grouped picks the shared-memory kernel), give bp_decode's
+    outputs."""
     import torch
 
     dev = gpu_device()
     sizes = [(2048, 0.5), (1024, 0.5), (512, 0.75), (256, 0.5), (128, 0.5)]
     parts, _ = make_parts(pcbp, oracle, dev, sizes, 250, seed=13)
     want = per_batch(pcbp, parts)
-    for wide in (False, True):
+    for kernel in (0, 1):
+        if kernel == 1:
+            monkeypatch.setenv("PCBP_DECODER", "grouped")
         chosen = []
         for code, sch, max_iters, llr, slots in parts:
-            N = code.N
-            tpf = max(32, N // 4) if (wide or N < 256) else N // 8
-            chosen.append((code, sch, max_iters, llr, slots, tpf))
+            chosen.append((code, sch, max_iters, llr, slots, pcbp.bp_kernel_threads(code, kernel)))
         md = pcbp.MixedDecoder(chosen, dev)
         bits, iters, ok = md()
         torch.cuda.synchronize()
         for i in range(len(parts)):
-            assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1]), (sizes[i], wide)
+            assert torch.equal(bits[i], want[i][0]) and torch.equal(iters[i], want[i][1]), (sizes[i], kernel)
             assert torch.equal(ok[i], want[i][2])
 
 
@@ -152,7 +154,7 @@ def test_slot_limit_is_what_a_launch_uses(pcbp, oracle):
     parts, _ = make_parts(pcbp, oracle, dev, sizes, 200, seed=29)
     for code, sch, max_iters, llr, _ in parts:
         N = code.N
-        for tpf in sorted({max(32, N // 4)} | ({N // 8} if N >= 256 else set())):
+        for tpf in sorted({t for t in (pcbp.bp_kernel_threads(code, k) for k in (0, 1)) if t}):
             lim = pcbp.bp_slot_limit(code, tpf, int(sch.fkind))
             assert 1 <= lim <= 1024 // tpf
             outs = []
