@@ -150,9 +150,10 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def cpu_oracle(frames_budget_s: float, seed: int = 97):
-    """The oracle as it stands (FP32, OpenMP over frames) on host cores, on
-    chunks of the workload until the wall-time budget is used."""
+def cpu_oracle(frames_budget_s: float, seed: int = 97, threads: int = 0):
+    """The oracle as it stands (FP32, OpenMP over frames) on host cores (all of
+    them, or `threads`), on chunks of the workload until the wall-time budget is
+    used."""
     import numpy as np
 
     import oracle as O
@@ -160,7 +161,7 @@ def cpu_oracle(frames_budget_s: float, seed: int = 97):
 
     _, fr = O.construct(N, K)
     s = O.Sched(**{**SCHED, "alpha": 0.9375})
-    threads = O.max_threads()
+    threads = threads or O.max_threads()
     chunk = max(256, 64 * threads)
     done = bits = iters_sum = errs = 0
     elapsed = 0.0
@@ -728,11 +729,14 @@ def run_ours(args):
 
     if rank == 0 and not args.no_cpu:
         cb = cpu_oracle(args.cpu_seconds)
+        cb1 = cpu_oracle(min(3.0, args.cpu_seconds), seed=197, threads=1)
         line["cpu_baseline"] = {"value": cb["gbps"], "unit": "Gbit/s", "cores": cb["cores"], "kind": "oracle",
                                 "sample": f"{cb['frames']} frames of the same workload (fresh seeds), "
                                           f"{cb['seconds']:.1f} s",
                                 "fer": cb["fer"], "fer_ci95": wilson(cb["errors"], cb["frames"]),
-                                "mean_iters": cb["mean_iters"]}
+                                "mean_iters": cb["mean_iters"],
+                                "value_1core": cb1["gbps"],
+                                "sample_1core": f"{cb1['frames']} frames, {cb1['seconds']:.1f} s on 1 core"}
         lo, hi_ = line["cpu_baseline"]["fer_ci95"]
         line["fer_matched"] = bool(lo <= line["fer"] <= hi_ or line["fer_ci95"][0] <= cb["fer"] <= line["fer_ci95"][1])
     if rank == 0:
