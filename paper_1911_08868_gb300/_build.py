@@ -2,7 +2,7 @@
 
 The decoder kernels are instantiated once per code length from
 ``csrc/bp_inst.cu`` and ``csrc/bp_inst2.cu`` (n = 3..11) and
-``csrc/bp_inst3.cu`` (n = 8..11); those translation units compile in
+``csrc/bp_inst3.cu`` (n = 7..11); those translation units compile in
 parallel.  Objects go
 to ``_build/`` at the repository root; the library is written next to this
 file.  A rebuild only recompiles objects older than their sources or any

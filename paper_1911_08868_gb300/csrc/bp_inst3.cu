@@ -1,6 +1,6 @@
 // Instantiates the TMEM-resident stage-grouped decoder kernel for one code
-// length, 2^PCBP_LOGN (compiled once per n = 8..11: every lane of a warp owns
-// 2^KB positions from N = 256 on).
+// length, 2^PCBP_LOGN (compiled once per n = 7..11: every lane of a warp owns
+// 2^KB positions, KB = tmem_default_kb(n) unless PCBP_KB3 sets it).
 #include "bp_kernel3.cuh"
 #include "bp_launch.h"
 

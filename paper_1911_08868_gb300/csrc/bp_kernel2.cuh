@@ -1,5 +1,5 @@
 // Stage-grouped PP-BP decoder kernel for sm_103a (Algorithm 1 of arXiv
-// 1911.08868): the bp_decode path for N < 256 (and for every N when
+// 1911.08868): the bp_decode path for N < 128 (and for every N when
 // PCBP_DECODER=grouped); its stage partition and swizzled planes are also the
 // base of the TMEM kernel (bp_kernel3.cuh).
 //

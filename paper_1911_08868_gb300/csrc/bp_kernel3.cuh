@@ -1,5 +1,5 @@
 // Stage-grouped PP-BP decoder kernel with group-private messages in tensor
-// memory (sm_103a TMEM), the bp_decode path for N >= 256 (Algorithm 1 of
+// memory (sm_103a TMEM), the bp_decode path for N >= 128 (Algorithm 1 of
 // arXiv 1911.08868).
 //
 // Positions per thread, swizzled shared-memory planes, stop tests and switch

@@ -1,8 +1,8 @@
 // Per-length launch entry points of the decoder kernels (one set per n):
 // bp_* from bp_inst.cu (per-stage kernel, used for the trace entry), bp2_*
-// from bp_inst2.cu (stage-grouped kernel, bp_decode for n < 8), bp3_* from
+// from bp_inst2.cu (stage-grouped kernel, bp_decode for n < 7), bp3_* from
 // bp_inst3.cu (stage-grouped kernel with TMEM-resident group interiors,
-// bp_decode for n = 8..11).
+// bp_decode for n = 7..11).
 #pragma once
 
 #include <cuda_runtime.h>

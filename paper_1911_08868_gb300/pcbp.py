@@ -280,7 +280,7 @@ class HostDecoder:
 
 def pc_partition_selfcheck(device="cuda"):
     """(partitions checked, event shapes whose two partition builds differ, partitions whose
-    group shape the sweeps do not assume) of the N >= 256 decoder."""
+    group shape the sweeps do not assume) of the N >= 128 decoder."""
     import torch
 
     out = torch.zeros(3, dtype=torch.int32, device=device)

@@ -1,7 +1,7 @@
 """bp_decode_host: the decoder reading page-locked host LLRs and writing its
 results into page-locked host memory in place.  Its outputs must equal the
-oracle's and bp_decode's bit for bit, for both decoder kernels (N < 256: the
-shared-memory kernel; N >= 256: the tensor-memory kernel), and buffers the
+oracle's and bp_decode's bit for bit, for both decoder kernels (N < 128: the
+shared-memory kernel; N >= 128: the tensor-memory kernel), and buffers the
 device cannot address must be refused before anything runs."""
 import numpy as np
 import pytest
@@ -12,6 +12,7 @@ from test_gpu_parity import POLY8, POLY24, frames, oracle_outputs, osched
 pytestmark = pytest.mark.gpu
 
 CASES = [
+    (64, 32, 8, POLY8, 2.5, dict(mode=1, rho_range_fixed=3, P_level=5, N_min=5, T0=5), 60, 400),
     (128, 64, 8, POLY8, 2.5, dict(mode=1, rho_range_fixed=3, P_level=6, N_min=5, T0=5), 60, 400),
     (1024, 512, 24, POLY24, 2.5, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10), 300, 300),
 ]
