@@ -73,9 +73,16 @@ def dist_env():
 
 
 def kernel_sha() -> str:
+    """Hash of the N = 1024 bp_decode kernel's sources with comments and white space removed, so
+    that the profiled traffic stays attached to the code it was measured on, not to its comments."""
+    import re
+
     h = hashlib.sha256()
-    for name in ("bp_kernel.cuh", "bp_kernel2.cuh", "bp_kernel3.cuh", "bp_inst3.cu"):   # the N = 1024 bp_decode kernel
-        h.update((ROOT / "paper_1911_08868_gb300" / "csrc" / name).read_bytes())
+    for name in ("bp_kernel.cuh", "bp_kernel2.cuh", "bp_kernel3.cuh", "bp_inst3.cu"):
+        text = (ROOT / "paper_1911_08868_gb300" / "csrc" / name).read_text()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:12]
 
 
