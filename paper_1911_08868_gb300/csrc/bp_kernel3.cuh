@@ -1014,12 +1014,26 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     if (lane == 0 && part) atomicXor(&ctl->crc_part[pb], part);
                 }
                 if (want_g) {
+                    if (!((rcL.x >> 24) & 1) && int((signed char)(rcL.z & 0xff)) == 0) {
+                        // the register bits are position bits 0..KB-1 (every thread in class 0,
+                        // in stage order): a thread's decisions lie in one E-bit field of the word
+                        // it shares with 32/E neighbouring lanes, combined by shuffles and stored once
+                        const int base = pos_of(AL[0], s0L);
+                        unsigned v = 0u;
 #pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if ((umask >> e) & 1u) {
-                            const int j = pos_of(AL[e], s0L);
-                            atomicOr(&dec[j >> 5], 1u << (j & 31));
-                        }
+                        for (int e = 0; e < E; ++e)
+                            if ((umask >> e) & 1u) v |= 1u << (pos_of(AL[e], s0L) & 31);
+#pragma unroll
+                        for (int o = 1; o < 32 / E; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+                        if ((lane & (32 / E - 1)) == 0) dec[base >> 5] = v;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if ((umask >> e) & 1u) {
+                                const int j = pos_of(AL[e], s0L);
+                                atomicOr(&dec[j >> 5], 1u << (j & 31));
+                            }
+                    }
                 }
                 // R sweep of the last group (ahead of the stop test)
                 tm_wait_st();
@@ -1106,6 +1120,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                             } else if (!FIRST) {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
+                            } else if (!((rc.x >> 24) & 1) && int((signed char)(rc.z & 0xff)) == n - KB) {
+                                // the register bits are the top KB position bits (every thread in
+                                // class 0), so the lanes are position bits 0..4: per register, one
+                                // ballot is a whole word of the hard decisions x_j = [L1 + R1 < 0]
+#pragma unroll
+                                for (int e = 0; e < E; ++e) {
+                                    const unsigned w = __ballot_sync(0xffffffffu, __fadd_rn(L1[e], y[e]) < 0.f);
+                                    if (lane == 0) xh[pos_of(A[e], 0) >> 5] = w;
+                                }
                             } else {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) {
