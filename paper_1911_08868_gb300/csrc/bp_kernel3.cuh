@@ -858,7 +858,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         const float* llr_f = J.llr + size_t(f) * N;
 
         for (int i = tid; i < NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = tid; i < NW; i += T) dec[i] = 0u;
+        for (int i = tid; i < NW; i += T) {
+            dec[i] = 0u;
+            xh[i] = 0u;
+        }
         if (fresh) {
             // the partition is still the no-event one; only the residues restart
             if (tid == 0) {
@@ -883,12 +886,6 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         int pb = 0;     // it % 3
         for (int it = 1; it <= max_iters; ++it) {
             pb = pb == 2 ? 0 : pb + 1;
-            if (want_g) {
-                for (int i = tid; i < NW; i += T) {
-                    xh[i] = 0u;
-                    dec[i] = 0u;
-                }
-            }
             const int ng = ctl->g.ng;
             const int lowmask = (1 << ctl->g.low) - 1;
             const int beta = ctl->g.beta;
@@ -950,7 +947,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         body(std::integral_constant<int, KB>{});
                     }
                 }
-                if (!want_g && ((rc.x >> 25) & 1)) __syncwarp();
+                if ((rc.x >> 25) & 1) __syncwarp();
                 else sync();
             };
             // single stages exist only while the event spans fewer than KB stages
@@ -1150,10 +1147,11 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     }
                 }
                 // group 0 writes shared state (the G-matrix bits) only for the G-matrix test
-                if (want_g) sync();
-                else if (!FIRST) {
+                if (!FIRST) {
                     if ((rc.x >> 26) & 1) __syncwarp();
                     else sync();
+                } else if (want_g) {
+                    sync();
                 }
             };
             if (!singles) {
@@ -1175,13 +1173,20 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     }
                     sync();
                     stop = (!want_crc || res == 0u) && ctl->g.g_ok != 0;
-                    sync();             // every thread has read g_ok before it is written again
                 }
                 if (stop) {
                     used = it;
                     break;
                 }
                 if (it == max_iters) break;
+                // the decision words restart empty for the next iteration: their writers and readers
+                // of this one are past the barriers above; the barrier below orders the clearing
+                // before the next writes, and every read of g_ok before its next write
+                for (int i = tid; i < NW; i += T) {
+                    xh[i] = 0u;
+                    dec[i] = 0u;
+                }
+                sync();
             }
 
             // a6: switch at iter == N_it,reset
