@@ -266,6 +266,16 @@ int bp_mixed_table_size(int32_t n_batches, size_t* bytes);
  * batch, PC_ENOMEM when bytes is too small; queries the device only after
  * every batch is valid. */
 int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void* h_table, size_t bytes);
+/* Build flags (host only; no counterpart in the paper): bit 0 set for a
+ * library built with PCBP_CHECKED, whose tensor-memory decoder kernel
+ * range-checks every shared-memory plane access, TMEM column, channel-LLR
+ * index and decision-word index.  In such a build bp_decode clears 32 bytes of
+ * its workspace and an access out of range of class c (0 plane offset, 1 TMEM
+ * column, 2 decided position, 3 position at a partition change, 4 reset
+ * index, 5 single-stage index) sets bit c of the uint32 at byte 16 of the
+ * workspace and is redirected inside its buffer. */
+int pc_build_info(int32_t* flags);
+
 /* Threads per frame of a decoder kernel for this code (kernel 0: the kernel
  * with TMEM-resident stage groups, N = 128..2048, groups of 2 stages up to
  * N = 512 and of 3 from N = 1024, so N/4 or N/8; kernel 1: the shared-memory

@@ -20,7 +20,8 @@ PKG = Path(__file__).resolve().parent
 ROOT = PKG.parent
 CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
-BUILD = ROOT / "_build"
+CHECKED = os.environ.get("PCBP_CHECKED") == "1"   # bounds-checked decoder (debug build)
+BUILD = ROOT / ("_build_checked" if CHECKED else "_build")
 LIB = PKG / "libpcbp.so"
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -49,7 +50,7 @@ def _stale(obj: Path, src: Path) -> bool:
 def _jobs() -> list[tuple[Path, Path, list[str]]]:
     nvcc = _nvcc()
     common = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
-              f"-I{INCLUDE}", f"-I{CSRC}"]
+              f"-I{INCLUDE}", f"-I{CSRC}", *(["-DPCBP_CHECKED"] if CHECKED else [])]
     jobs = []
     for n in LOGNS:
         obj = BUILD / f"bp_inst_{n}.o"
@@ -98,7 +99,7 @@ def build(verbose: bool = False, force: bool = False) -> Path:
                 if verbose and msg:
                     print(msg)
     objs = [str(j[0]) for j in jobs]
-    stamp = BUILD / "link_inputs.txt"          # relink when the set of objects changes
+    stamp = LIB.with_name(LIB.name + ".inputs")   # relink when the set of objects changes (checked <-> normal)
     same_set = stamp.exists() and stamp.read_text() == "\n".join(objs)
     if (force or todo or not same_set or not LIB.exists()
             or any(Path(o).stat().st_mtime > LIB.stat().st_mtime for o in objs)):

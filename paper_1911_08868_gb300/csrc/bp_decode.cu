@@ -366,7 +366,13 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     if (rc != PC_OK) return rc;
     P->slots = g.slots;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+#ifdef PCBP_CHECKED
+    // bound-check status word at byte 16 of the workspace (read back by the caller)
+    P->job.check = reinterpret_cast<unsigned*>(static_cast<unsigned char*>(d_workspace) + 16);
+    if (cudaMemsetAsync(d_workspace, 0, 32, st) != cudaSuccess) return PC_ECUDA;
+#else
     if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
+#endif
     const cudaError_t e = trace  ? launch_of(code->n, *P, g, true, sched->fkind, st)
                           : tmem ? launch3_of(code->n, *P, g, sched->fkind, st, false)
                                  : launch2_of(code->n, *P, g, sched->fkind, st, false);
@@ -589,6 +595,17 @@ extern "C" int bp_mixed_prepare(const pc_batch* batches, int32_t n_batches, void
         m->magic = kMixedMagic;
         std::memcpy(static_cast<MixedEntry*>(h_table) + i, m.get(), sizeof(MixedEntry));
     }
+    return PC_OK;
+}
+
+extern "C" int pc_build_info(int32_t* flags)
+{
+    if (!flags) return PC_EINVAL;
+#ifdef PCBP_CHECKED
+    *flags = 1;
+#else
+    *flags = 0;
+#endif
     return PC_OK;
 }
 

@@ -70,6 +70,15 @@
 
 namespace pcbp {
 
+// Builds with PCBP_CHECKED range-check every shared-memory plane access, TMEM
+// column, channel-LLR index and decision-word index of this kernel; an access
+// out of range sets bit `cls` of the status word (when there is one) and is
+// redirected inside the buffer, so nothing faults.
+__device__ __forceinline__ void chk_fail(unsigned* status, unsigned cls)
+{
+    if (status) atomicOr(status, 1u << cls);
+}
+
 // TMEM columns of one group's interior messages (E per level): group 0 skips
 // L level 1 (registers), the last group keeps its L in registers.
 __host__ __device__ constexpr int group_cols(int s0, int gl, bool single, bool last, int E)
@@ -602,7 +611,7 @@ __device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S,
 template <int LOGN, int E, int T, int FK>
 __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowmask, int beta, int lo, int m1, int pbit,
                                           const float* llr_f, float* Lp, float* Rp, uint32_t* xh,
-                                          const unsigned char* s_swz, float alpha)
+                                          const unsigned char* s_swz, float alpha, unsigned* check)
 {
     constexpr int n = LOGN;
     constexpr int N = 1 << LOGN;
@@ -614,6 +623,14 @@ __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowm
         if (s >= lo && s <= m1 && (q & lowmask) == beta) p = pbit;
         const int t = ((q >> p) << (p + 1)) | (q & ((1 << p) - 1));
         const int b = t | (1 << p);
+#ifdef PCBP_CHECKED
+        if (t >= N || b >= N || p < 0 || p >= n || s < 0 || s >= n - 1) {
+            chk_fail(check, 5);
+            continue;
+        }
+#else
+        (void)check;
+#endif
         const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
         const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
         const float rt = Rp[s * N + sw(t)];
@@ -718,9 +735,37 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     // byte offset (from smem) of the position in L plane s0-1 (node level
     // s0+1); the group's other planes are at fixed distances:
     //   Lp plane s0-1+d at A + 4 d N,   Rp plane s0-1+d at A + 4 (NPL + d) N.
-    auto at = [&](int a, int floats) -> float& { return *reinterpret_cast<float*>(smem + a + 4 * floats); };
+    auto at = [&](int a, int floats) -> float& {
+        int off = a + 4 * floats;
+#ifdef PCBP_CHECKED
+        if (off < lp_off || off > lp_off + 4 * (2 * NPL * N - 1) || (off & 3)) {
+            chk_fail(J.check, 0);
+            off = lp_off;
+        }
+#endif
+        return *reinterpret_cast<float*>(smem + off);
+    };
+    // TMEM address of column `col` of this thread's bank
+    auto tc = [&](uint32_t col) -> uint32_t {
+#ifdef PCBP_CHECKED
+        if (col > uint32_t(Geo::TCOLS - E)) {
+            chk_fail(J.check, 1);
+            col = 0;
+        }
+#endif
+        return tm + col;
+    };
     // logical position of cached offset a in a group with first stage s0
-    auto pos_of = [&](int a, int s0) { return sw(((a - lp_off) >> 2) - (s0 - 1) * N); };
+    auto pos_of = [&](int a, int s0) {
+        int x = ((a - lp_off) >> 2) - (s0 - 1) * N;
+#ifdef PCBP_CHECKED
+        if (x < 0 || x >= N) {
+            chk_fail(J.check, 2);
+            x = 0;
+        }
+#endif
+        return sw(x);
+    };
 
     const DevSched& S = J.S;
     const float alpha = S.alpha;
@@ -751,10 +796,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if ((rc.x >> 16) & 1) continue;
             const uint32_t colR = uint32_t(rc.y + gl * E);
             #pragma unroll 1
-            for (int i = 0; i < gl - 1; ++i) tm_st<E>(tm + colR + uint32_t(i * E), z);
+            for (int i = 0; i < gl - 1; ++i) tm_st<E>(tc(colR + uint32_t(i * E)), z);
             if (gi == 0) {
                 int A[E];
-                tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                tm_ld_i<E>(tc(uint32_t(rc.w)), A);
                 tm_wait_ld();
                 tm_fence<E>(A);
 #pragma unroll
@@ -777,16 +822,24 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if ((rc.x >> 16) & 1) continue;
             int ph[E], A[E];
             group_offsets<LOGN, KB>(ctl, s_swz, gi, group_class(rc.x), rc.z, tid, ph);
+#ifdef PCBP_CHECKED
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (ph[e] < 0 || ph[e] >= N) {
+                    chk_fail(J.check, 3);
+                    ph[e] = 0;
+                }
+#endif
 #pragma unroll
             for (int e = 0; e < E; ++e) A[e] = lp_off + 4 * ((s0 - 1) * N + ph[e]);
-            tm_st_i<E>(tm + uint32_t(rc.w), A);
+            tm_st_i<E>(tc(uint32_t(rc.w)), A);
             const uint32_t colR = uint32_t(rc.y + gl * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {     // R level s0+2+i: Rp plane s0+i
                 float v[E];
 #pragma unroll
                 for (int e = 0; e < E; ++e) v[e] = at(A[e], (NPL + i + 1) * N);
-                tm_st<E>(tm + colR + uint32_t(i * E), v);
+                tm_st<E>(tc(colR + uint32_t(i * E)), v);
             }
             if (gi == ng - 1) {
                 float pr[E];
@@ -797,8 +850,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     pr[e] = prior_of(s_frozen, j);
                     cj[e] = int(s_cj[j]);
                 }
-                tm_st<E>(tm + uint32_t(Geo::PCOL), pr);
-                tm_st_i<E>(tm + uint32_t(Geo::CCOL), cj);
+                tm_st<E>(tc(uint32_t(Geo::PCOL)), pr);
+                tm_st_i<E>(tc(uint32_t(Geo::CCOL)), cj);
             }
             if (gi == 0) {
 #pragma unroll
@@ -818,14 +871,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if ((rc.x >> 16) & 1) continue;
             if (gl < 2) continue;
             int A[E];
-            tm_ld_i<E>(tm + uint32_t(rc.w), A);
+            tm_ld_i<E>(tc(uint32_t(rc.w)), A);
             tm_wait_ld();
             tm_fence<E>(A);
             const uint32_t colR = uint32_t(rc.y + gl * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {
                 float v[E];
-                tm_ld<E>(tm + colR + uint32_t(i * E), v);
+                tm_ld<E>(tc(colR + uint32_t(i * E)), v);
                 tm_wait_ld();
                 tm_fence<E>(v);
 #pragma unroll
@@ -903,17 +956,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     // one permuted stage with per-PE addressing (m < KB events)
                     single_stage<LOGN, E, T, FK>(false, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                  ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp, Rp,
-                                                 xh, s_swz, alpha);
+                                                 xh, s_swz, alpha, J.check);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
                         constexpr int GL = decltype(glc)::value;
                         int A[E];
                         float rp[GL > 1 ? GL - 1 : 1][E];
-                        tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                        tm_ld_i<E>(tc(uint32_t(rc.w)), A);
                         if constexpr (GL > 1) {
 #pragma unroll
-                            for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tm + colL + uint32_t((GL + i) * E), rp[i]);
+                            for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tc(colL + uint32_t((GL + i) * E)), rp[i]);
                         }
                         tm_wait_ld();
                         tm_fence<E>(A);
@@ -927,11 +980,11 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #pragma unroll
                             for (int i = 0; i < GL - 1; ++i) tm_fence<E>(rp[i]);
                         }
-                        if constexpr (!FIRST) tm_st<E>(tm + colL, x);       // L level s0+1
+                        if constexpr (!FIRST) tm_st<E>(tc(colL), x);       // L level s0+1
 #pragma unroll
                         for (int i = 0; i < GL; ++i) {
                             l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
-                            if (i < GL - 1) tm_st<E>(tm + colL + uint32_t((i + 1) * E), x);   // L level s0+2+i
+                            if (i < GL - 1) tm_st<E>(tc(colL + uint32_t((i + 1) * E)), x);   // L level s0+2+i
                         }
 #pragma unroll
                         for (int e = 0; e < E; ++e) at(A[e], GL * N) = x[e];          // L level s0+GL+1
@@ -978,11 +1031,11 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 float xL[GLL][E];
                 float x[E];
                 int cj[E];
-                tm_ld_i<E>(tm + uint32_t(rcL.w), AL);
-                tm_ld<E>(tm + uint32_t(Geo::PCOL), pr);
-                tm_ld_i<E>(tm + uint32_t(Geo::CCOL), cj);
+                tm_ld_i<E>(tc(uint32_t(rcL.w)), AL);
+                tm_ld<E>(tc(uint32_t(Geo::PCOL)), pr);
+                tm_ld_i<E>(tc(uint32_t(Geo::CCOL)), cj);
 #pragma unroll
-                for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tm + colLL + uint32_t((GLL + i) * E), rp[i]);
+                for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tc(colLL + uint32_t((GLL + i) * E)), rp[i]);
                 tm_wait_ld();
                 tm_fence<E>(AL);
                 tm_fence<E>(pr);
@@ -1041,7 +1094,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 for (int i = GLL - 1; i >= 0; --i) {
                     r_layer<E, FK>(y, xL[i], i, alpha);
                     if (i > 0) {
-                        tm_st<E>(tm + colLL + uint32_t((GLL + i - 1) * E), y);   // R level s0L+1+i
+                        tm_st<E>(tc(colLL + uint32_t((GLL + i - 1) * E)), y);   // R level s0L+1+i
                     } else {
 #pragma unroll
                         for (int e = 0; e < E; ++e) at(AL[e], NPL * N) = y[e];   // R level s0L+1
@@ -1086,17 +1139,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     if (!FIRST || want_g)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                      ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
-                                                     Rp, xh, s_swz, alpha);
+                                                     Rp, xh, s_swz, alpha, J.check);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
                         constexpr int GL = decltype(glc)::value;
                         int A[E];
                         float lv[GL][E];
-                        tm_ld_i<E>(tm + uint32_t(rc.w), A);
+                        tm_ld_i<E>(tc(uint32_t(rc.w)), A);
 #pragma unroll
                         for (int i = 0; i < GL; ++i)
-                            if (i > 0 || !FIRST) tm_ld<E>(tm + colL + uint32_t(i * E), lv[i]);   // L level s0+1+i
+                            if (i > 0 || !FIRST) tm_ld<E>(tc(colL + uint32_t(i * E)), lv[i]);   // L level s0+1+i
                         tm_wait_ld();
                         tm_fence<E>(A);
                         float y[E];
@@ -1113,7 +1166,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                             if (FIRST && i == 0 && !want_g) continue;      // stage 0 writes only the G-matrix bits
                             r_layer<E, FK>(y, lv[i], i, alpha);
                             if (i > 0) {
-                                tm_st<E>(tm + colL + uint32_t((GL + i - 1) * E), y);            // R level s0+1+i
+                                tm_st<E>(tc(colL + uint32_t((GL + i - 1) * E)), y);            // R level s0+1+i
                             } else if (!FIRST) {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
@@ -1219,8 +1272,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         const int span = 1 << m;
                         for (int i = tid; i < (rg - 1) * span; i += T) {
                             const int lev = lv + 1 + i / span;       // node level, 2..n
-                            const int j = int(bk) + ((i & (span - 1)) << (n - m));
-                            Rp[(lev - 2) * N + sw(j)] = 0.f;
+                            int j = int(bk) + ((i & (span - 1)) << (n - m));
+                            int plane = lev - 2;
+#ifdef PCBP_CHECKED
+                            if (j < 0 || j >= N || plane < 0 || plane >= NPL) {
+                                chk_fail(J.check, 4);
+                                j = 0;
+                                plane = 0;
+                            }
+#endif
+                            Rp[plane * N + sw(j)] = 0.f;
                         }
                     }
                     next_reset = it + ctl->g.next_inc;

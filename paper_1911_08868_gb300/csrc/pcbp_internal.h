@@ -49,6 +49,7 @@ struct FrameJob {
     int64_t B;
     int32_t max_iters;
     int32_t K, r;
+    unsigned* check;   // builds with PCBP_CHECKED: bit c set when an access of class c was out of range (nullable)
 };
 
 struct DevEvent {

@@ -21,7 +21,8 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_host", "bp_decode_trace",
-            "bp_decode_noalloc", "pc_partition_selfcheck", "bp_kernel_threads", "bp_slot_limit", "bp_mixed_table_size",
+            "bp_decode_noalloc", "pc_partition_selfcheck", "pc_build_info", "bp_kernel_threads", "bp_slot_limit",
+            "bp_mixed_table_size",
             "bp_mixed_prepare",
             "bp_mixed_workspace_size",
             "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
@@ -78,6 +79,7 @@ _lib.bp_mixed_workspace_size.argtypes = [C.c_int32, C.POINTER(C.c_size_t)]
 _lib.bp_decode_mixed.argtypes = [_vp, C.c_int32, _vp, _vp]
 _lib.bp_slot_limit.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
 _lib.bp_kernel_threads.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_int32)]
+_lib.pc_build_info.argtypes = [C.POINTER(C.c_int32)]
 _lib.wbp_weights_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.POINTER(C.c_size_t)]
 _lib.wbp_ckpt_count.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.POINTER(C.c_size_t)]
 _lib.wbp_workspace_size.argtypes = [C.POINTER(PcCode), C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_size_t)]
@@ -287,6 +289,13 @@ def pc_partition_selfcheck(device="cuda"):
     _check("pc_partition_selfcheck", _lib.pc_partition_selfcheck(_ptr(out), _stream(None)))
     torch.cuda.synchronize()
     return int(out[0].item()), int(out[1].item()), int(out[2].item())
+
+
+def build_checked() -> bool:
+    """True for a library built with PCBP_CHECKED (bounds-checked decoder)."""
+    out = C.c_int32(0)
+    _check("pc_build_info", _lib.pc_build_info(C.byref(out)))
+    return bool(out.value & 1)
 
 
 def bp_kernel_threads(code: PcCode, kernel: int):
