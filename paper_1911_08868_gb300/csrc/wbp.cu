@@ -91,6 +91,30 @@ __device__ __forceinline__ void bar(unsigned id, unsigned count)
 __device__ __forceinline__ float2 ld_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
 __device__ __forceinline__ double2 ld_pair(const double* p) { return __ldg(reinterpret_cast<const double2*>(p)); }
 
+// Copy count reals from global to shared memory with cp.async (every element
+// in flight at once, no register round trip): 16-byte pieces when both ends
+// are 16-byte aligned and the size is a multiple of 16, else one real each.
+// The caller waits with copy_wait() and then synchronises the slot.
+template <typename Real>
+__device__ __forceinline__ void copy_async(Real* dst, const Real* src, int count, int tid, int tps)
+{
+    const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
+    const size_t g = size_t(__cvta_generic_to_global(src));
+    const size_t bytes = size_t(count) * sizeof(Real);
+    if (((g | size_t(d) | bytes) & 15u) == 0) {
+        for (int i = tid; i < int(bytes / 16); i += tps)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * uint32_t(i)), "l"(g + 16u * size_t(i))
+                         : "memory");
+    } else {
+        for (int i = tid; i < count; i += tps)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d + uint32_t(sizeof(Real)) * uint32_t(i)),
+                         "l"(g + sizeof(Real) * size_t(i)), "n"(int(sizeof(Real)))
+                         : "memory");
+    }
+}
+
+__device__ __forceinline__ void copy_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <typename Real>
 __device__ __forceinline__ Real prior_v(const uint32_t* frozen, int j)
 {
@@ -127,10 +151,11 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
         bar(bid, tps);
         const long long f = s_frame[slot];
         if (f >= P.B) break;
-        for (int j = tid; j < N; j += tps) L[j] = P.llr[size_t(f) * N + j];
+        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
         for (int j = tid; j < (n - 1) * N; j += tps) R[j] = Real(0);
         if (P.ckpt)
             for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = Real(0);
+        copy_wait();
         bar(bid, tps);
         for (int it = 0; it < P.T; ++it) {
             const Real* wt = P.w + size_t(it) * wplane;
@@ -166,9 +191,10 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
                 bar(bid, tps);
             }
             if (P.ckpt) {
+                // no barrier after the copy: the R planes are next written by the R sweep of
+                // the next iteration, n slot barriers later
                 Real* dst = P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N;
                 for (int j = tid; j < (n - 1) * N; j += tps) dst[j] = R[j];
-                bar(bid, tps);
             }
         }
         for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[n * N + s_info[k]];
@@ -219,14 +245,13 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
         const long long f = s_frame[slot];
         if (f >= P.B) break;
         const Real* Rp = P.ckpt + (size_t(it) * P.B + size_t(f)) * (n - 1) * N;   // R(it) before this iteration
-        auto load_rp = [&]() {
-#pragma unroll 4
-            for (int j = tid; j < (n - 1) * N; j += tps) Rt[j] = Rp[j];
-        };
+        // R(it) and the channel LLRs stream into their planes while the gradient planes are cleared
+        auto load_rp = [&]() { copy_async(Rt, Rp, (n - 1) * N, tid, tps); };
         load_rp();
-        for (int j = tid; j < N; j += tps) L[j] = P.llr[size_t(f) * N + j];
+        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
         for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = Real(0);
         for (int j = tid; j < N; j += tps) gA[j] = gB[j] = Real(0);
+        copy_wait();
         bar(bid, tps);
         // forward recomputation of iteration it
         for (int s = 0; s < n; ++s) {
@@ -317,6 +342,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
         // adjoint of the L sweep: stage s makes L level s+2 from L level s+1 and R(it) level s+2
         if (!last) {                  // the R planes hold R(it+1): R(it) again
             load_rp();
+            copy_wait();
             bar(bid, tps);
         }
         Real* gout = P.gout + size_t(f) * (n - 1) * N;
