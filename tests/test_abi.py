@@ -44,6 +44,17 @@ def test_library_exports_every_declared_symbol(pcbp):
     assert set(pcbp.EXPORTED) <= set(names)
 
 
+def test_build_info_reports_the_checked_build(pcbp):
+    """pc_build_info bit 0 is set exactly for a library built with PCBP_CHECKED=1 (the build the
+    tests load follows the same environment variable)."""
+    import os
+
+    assert pcbp.build_checked() == (os.environ.get("PCBP_CHECKED") == "1")
+    lib = C.CDLL(pcbp.library_path())
+    lib.pc_build_info.argtypes = [C.c_void_p]
+    assert lib.pc_build_info(None) == pcbp.PC_EINVAL
+
+
 @pytest.mark.parametrize("N,K,db", [(8, 4, 0.0), (64, 32, 0.0), (256, 128, 0.0), (1024, 512, 0.0),
                                     (2048, 1024, 0.0), (512, 384, 1.5), (128, 32, -2.0), (2048, 1536, 0.0)])
 def test_pc_construct_matches_oracle(pcbp, oracle, N, K, db):
