@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
 // Shared memory per frame slot: L at levels 1..n+1, R at levels 2..n+1 (level
 // n+1: the priors, written once per CTA), the gradient of L at levels 1..n+1
 // and two planes for the gradient flowing between R levels.  The R planes hold
-// R before this iteration (copied from the checkpoint in one coalesced pass)
+// R before this iteration (copied from the checkpoint with cp.async)
 // for the L sweep, R after it (recomputed in place, as in the forward kernel)
 // for the adjoint of the R sweep, and R before it again (a second copy) for
 // the adjoint of the L sweep.
