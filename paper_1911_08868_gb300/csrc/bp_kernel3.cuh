@@ -79,6 +79,29 @@ __device__ __forceinline__ void chk_fail(unsigned* status, unsigned cls)
     if (status) atomicOr(status, 1u << cls);
 }
 
+// Register-to-position bit maps of the two G-matrix fast paths (the register
+// bits of build_partition_warp for a group of natural stage order):
+// the last group of GL stages ends at stage n-1, so register bit i < GL is
+// position bit GL-1-i and the filled bits GL..KB-1 are themselves; group 0's
+// register bit i is position bit n-1-i.
+template <int GL, int KB>
+__host__ __device__ constexpr int last_group_offset(int e)
+{
+    int off = 0;
+    for (int i = 0; i < KB; ++i)
+        if ((e >> i) & 1) off |= 1 << (i < GL ? GL - 1 - i : i);
+    return off;
+}
+
+template <int KB>
+__host__ __device__ constexpr int reverse_bits(int e)
+{
+    int r = 0;
+    for (int i = 0; i < KB; ++i)
+        if ((e >> i) & 1) r |= 1 << (KB - 1 - i);
+    return r;
+}
+
 // TMEM columns of one group's interior messages (E per level): group 0 skips
 // L level 1 (registers), the last group keeps its L in registers.
 __host__ __device__ constexpr int group_cols(int s0, int gl, bool single, bool last, int E)
@@ -1053,10 +1076,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 // a5: decisions u_j = [L(n+1) + R(n+1) < 0], taken as L(n+1) < -R(n+1) (a
                 // rounded sum has the sign of the exact one), and their CRC residue
                 unsigned part = 0;
+                unsigned pmask = 0;     // G-matrix test: the decisions at their position bits within the block
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const bool u = x[e] < -pr[e];
                     umask |= u ? 1u << e : 0u;
+                    if constexpr (want_g) pmask |= u ? 1u << last_group_offset<GLL, KB>(e) : 0u;
                     part ^= u ? unsigned(cj[e]) : 0u;
                 }
                 if (check && want_crc) {
@@ -1068,11 +1093,9 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         // the register bits are position bits 0..KB-1 (every thread in class 0,
                         // in stage order): a thread's decisions lie in one E-bit field of the word
                         // it shares with 32/E neighbouring lanes, combined by shuffles and stored once
+                        // (register e at position base + last_group_offset(e), base E-aligned)
                         const int base = pos_of(AL[0], s0L);
-                        unsigned v = 0u;
-#pragma unroll
-                        for (int e = 0; e < E; ++e)
-                            if ((umask >> e) & 1u) v |= 1u << (pos_of(AL[e], s0L) & 31);
+                        unsigned v = pmask << (base & 31);
 #pragma unroll
                         for (int o = 1; o < 32 / E; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
                         if ((lane & (32 / E - 1)) == 0) dec[base >> 5] = v;
@@ -1174,10 +1197,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                                 // the register bits are the top KB position bits (every thread in
                                 // class 0), so the lanes are position bits 0..4: per register, one
                                 // ballot is a whole word of the hard decisions x_j = [L1 + R1 < 0]
+                                // (register e adds reverse_bits(e) << (n - KB) to the position, so
+                                // reverse_bits(e) << (n - KB - 5) to lane 0's word)
+                                const int w0 = pos_of(A[0], 0) >> 5;
 #pragma unroll
                                 for (int e = 0; e < E; ++e) {
                                     const unsigned w = __ballot_sync(0xffffffffu, __fadd_rn(L1[e], y[e]) < 0.f);
-                                    if (lane == 0) xh[pos_of(A[e], 0) >> 5] = w;
+                                    if (lane == 0) xh[w0 | (reverse_bits<KB>(e) << (n - KB - 5))] = w;
                                 }
                             } else {
 #pragma unroll
