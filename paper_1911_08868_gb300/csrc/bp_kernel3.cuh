@@ -93,6 +93,16 @@ __host__ __device__ constexpr int last_group_offset(int e)
     return off;
 }
 
+// The E decision bits of a thread (bit e for register e) at their position bits in the thread's block.
+template <int GL, int KB>
+__device__ __forceinline__ unsigned last_group_bits(unsigned umask)
+{
+    unsigned v = 0u;
+#pragma unroll
+    for (int e = 0; e < (1 << KB); ++e) v |= ((umask >> e) & 1u) << last_group_offset<GL, KB>(e);
+    return v;
+}
+
 template <int KB>
 __host__ __device__ constexpr int reverse_bits(int e)
 {
@@ -1137,15 +1147,29 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 const bool stop = check && res == 0u;
                 if (stop || it == max_iters) {
                     fetch_next();
-                    // the decision words, once per frame
-                    for (int i = tid; i < NW; i += T) dec[i] = 0u;
-                    sync();
+                    // the decision words, once per frame: where every thread's register bits are
+                    // position bits 0..KB-1 (class 0, in stage order), 32/E neighbouring lanes
+                    // combine one whole word by shuffles; otherwise one shared atomic per decided
+                    // position into cleared words
+                    if (!((rcL.x >> 24) & 1) && int((signed char)(rcL.z & 0xff)) == 0) {
+                        const unsigned pm = glL == KB ? last_group_bits<KB, KB>(umask)
+                                            : (KB > 2 && glL == 2) ? last_group_bits<(KB > 2 ? 2 : 1), KB>(umask)
+                                                                   : last_group_bits<1, KB>(umask);
+                        const int base = pos_of(AL[0], s0L);
+                        unsigned v = pm << (base & 31);
 #pragma unroll
-                    for (int e = 0; e < E; ++e)
-                        if ((umask >> e) & 1u) {
-                            const int j = pos_of(AL[e], s0L);
-                            atomicOr(&dec[j >> 5], 1u << (j & 31));
-                        }
+                        for (int o = 1; o < 32 / E; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+                        if ((lane & (32 / E - 1)) == 0) dec[base >> 5] = v;
+                    } else {
+                        for (int i = tid; i < NW; i += T) dec[i] = 0u;
+                        sync();
+#pragma unroll
+                        for (int e = 0; e < E; ++e)
+                            if ((umask >> e) & 1u) {
+                                const int j = pos_of(AL[e], s0L);
+                                atomicOr(&dec[j >> 5], 1u << (j & 31));
+                            }
+                    }
                     sync();
                     if (stop) used = it;
                     break;
