@@ -331,13 +331,16 @@ VARIANTS = {
     "ppbp_crc_and_g": dict(SCHED, stop_kind=3),
     # exact box-plus f
     "ppbp_boxplus": dict(SCHED, fkind=1),
+    # the stop test applied from iteration 5 only (Sec. IV skips "the first few" iterations)
+    "ppbp_stop_from5": dict(SCHED, stop_from=5),
 }
 VARIANT_MAX_ITERS = {"fpbp_q10_t100": 1000}
 
 
 def run_variants(pcbp, inputs, dev, warmup):
     """Throughput, FER and mean iterations of the other schedules of the same code on the same
-    2^17 frames (Eb/N0 3.0 dB): FP-BP, plain BP, unscaled min-sum, CRC + G-matrix stop, box-plus."""
+    2^17 frames (Eb/N0 3.0 dB): FP-BP, plain BP, unscaled min-sum, CRC + G-matrix stop, box-plus,
+    the stop test from iteration 5."""
     import torch
 
     B = VARIANT_FRAMES
