@@ -331,7 +331,7 @@ VARIANTS = {
     "ppbp_crc_and_g": dict(SCHED, stop_kind=3),
     # exact box-plus f
     "ppbp_boxplus": dict(SCHED, fkind=1),
-    # the stop test applied from iteration 5 only (Sec. IV skips "the first few" iterations)
+    # the stop test applied from iteration 5 only (Sec. IV leaves the number of untested first iterations open)
     "ppbp_stop_from5": dict(SCHED, stop_from=5),
 }
 VARIANT_MAX_ITERS = {"fpbp_q10_t100": 1000}

@@ -70,7 +70,7 @@ typedef struct {
  *   FP-BP: a new full stage order every it_reset_full iterations, at most
  *     q_max - 1 switches (q_max <= 0: unlimited).
  *   stop_from: first iteration at which the stop test is applied (Sec. IV
- *     skips "the first few" iterations); stop_kind bit 0 = CRC residue zero,
+ *     skips it in an unstated number of first iterations); stop_kind bit 0 = CRC residue zero,
  *     bit 1 = G-matrix test (u G_N equals the hard decisions of L1 + R1);
  *     0 = never stop early.
  *   fkind: 0 scaled min-sum f = alpha * sign * sign * min (alpha = 1 is the

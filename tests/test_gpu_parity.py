@@ -144,7 +144,7 @@ DECODE_CASES = [
     (1024, 512, 24, POLY24, 2.5, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10), 300, 300),
     (1024, 512, 24, POLY24, 2.0, dict(mode=2, it_reset_full=100, q_max=10), 1000, 60),
     (1024, 512, 24, POLY24, 2.5, dict(mode=1, P_range=2, P_level=6, D=8, N_min=4, T0=16, alpha=1.0), 200, 200),
-    # the stop test from iteration 5 only (Sec. IV leaves "the first few iterations" unquantified)
+    # the stop test from iteration 5 only (Sec. IV does not say how many first iterations skip it)
     (1024, 512, 24, POLY24, 3.0, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10, stop_from=5), 300, 300),
     (2048, 1024, 24, POLY24, 2.25, dict(mode=1, rho_range_fixed=3, P_level=10, N_min=5, T0=5, stop_kind=3), 100, 150),
 ]
