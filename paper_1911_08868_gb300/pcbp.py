@@ -22,11 +22,9 @@ PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_host", "bp_decode_trace",
             "bp_decode_noalloc", "pc_partition_selfcheck", "pc_build_info", "bp_kernel_threads", "bp_slot_limit",
-            "bp_mixed_table_size",
-            "bp_mixed_prepare",
-            "bp_mixed_workspace_size",
-            "bp_decode_mixed", "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward",
-            "wbp_backward", "wbp_forward_f64", "wbp_backward_f64", "pc_status_string")
+            "bp_mixed_table_size", "bp_mixed_prepare", "bp_mixed_workspace_size", "bp_decode_mixed",
+            "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward", "wbp_backward",
+            "wbp_forward_f64", "wbp_backward_f64", "pc_status_string")
 PC_MAX_BATCHES = 64
 PC_STATIC_SCRATCH_BYTES = 4096
 
@@ -106,6 +104,30 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _require(fn: str, *checks):
+    """Raise PcError(PC_EINVAL) unless every (tensor, dtype, shape, where) check holds: the C calls
+    receive bare pointers, so the tensors behind them must have the layout the call assumes.
+    where: "cuda" (device memory), "any" (device or host; the call checks host memory itself)."""
+    for t, dtype, shape, where in checks:
+        ok = (t is not None and t.dtype == dtype and tuple(t.shape) == tuple(shape) and t.is_contiguous()
+              and (where != "cuda" or t.is_cuda))
+        if not ok:
+            raise PcError(fn, PC_EINVAL)
+
+
+def _require_workspace(fn: str, ws, nbytes: int, where: str = "cuda"):
+    if ws is None or not ws.is_contiguous() or ws.numel() * ws.element_size() < nbytes or (where == "cuda" and not ws.is_cuda):
+        raise PcError(fn, PC_EINVAL)
+
+
+def _decode_checks(code, llr, bits, iters, crc_ok, where):
+    import torch
+
+    B = llr.shape[0] if llr is not None and llr.dim() == 2 else -1
+    return ((llr, torch.float32, (B, code.N), where), (bits, torch.int32, (B, words_of(code.K)), where),
+            (iters, torch.int32, (B,), where), (crc_ok, torch.uint8, (B,), where))
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -148,7 +170,11 @@ def pc_construct(N: int, K: int, crc_len: int = 0, crc_poly: int = 0, design_ebn
 
 def pc_encode(code: PcCode, payload, x_out, stream=None):
     """payload: uint8 CUDA tensor [B, K - crc_len]; x_out: uint8 CUDA tensor [B, N]."""
+    import torch
+
     B = x_out.shape[0]
+    _require("pc_encode", (payload, torch.uint8, (B, code.K - code.crc_len), "cuda"),
+             (x_out, torch.uint8, (B, code.N), "cuda"))
     _check("pc_encode", _lib.pc_encode(C.byref(code), _ptr(payload), _ptr(x_out), B, _stream(stream)))
 
 
@@ -159,8 +185,10 @@ def bp_decode_workspace_size(code: PcCode, B: int) -> int:
 
 
 def bp_decode(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, workspace, stream=None):
-    """llr: float32 [B, N]; bits: int32 [B, ceil(K/32)]; iters: int32 [B]; crc_ok: uint8 [B]."""
+    """llr: float32 [B, N]; bits: int32 [B, ceil(K/32)]; iters: int32 [B]; crc_ok: uint8 [B] (CUDA tensors)."""
     B = llr.shape[0]
+    _require("bp_decode", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"))
+    _require_workspace("bp_decode", workspace, bp_decode_workspace_size(code, B))
     _check("bp_decode", _lib.bp_decode(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
                                        _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
 
@@ -169,6 +197,8 @@ def bp_decode_host(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters,
     """bp_decode on tensors in page-locked host memory (or on the device): the kernel reads and
     writes them in place.  Asynchronous on the stream."""
     B = llr.shape[0]
+    _require("bp_decode_host", *_decode_checks(code, llr, bits, iters, crc_ok, "any"))
+    _require_workspace("bp_decode_host", workspace, bp_decode_workspace_size(code, B))
     _check("bp_decode_host", _lib.bp_decode_host(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
                                                  _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
 
@@ -176,7 +206,14 @@ def bp_decode_host(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters,
 def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dump, bits, iters, crc_ok, workspace,
                     stream=None):
     """As bp_decode, recording every plane into dump [B, max_iters, 2, n+1, N]; events: list of PcEvent or None."""
+    import torch
+
     B = llr.shape[0]
+    # the dump's layout is [B][max_iters][2][n+1][N]; with no iterations nothing is written
+    dump_shape = (B, max_iters, 2, code.n + 1, code.N) if max_iters > 0 else (tuple(dump.shape) if dump is not None else ())
+    _require("bp_decode_trace", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"),
+             (dump, torch.float32, dump_shape, "cuda"))
+    _require_workspace("bp_decode_trace", workspace, bp_decode_workspace_size(code, B))
     if events is None:
         evp, nev = None, 0
     else:
@@ -193,6 +230,7 @@ def bp_decode_noalloc(code: PcCode, llr, sch: PcSched, max_iters: int, bits, ite
     calls must not overlap on the GPU, and the first call on a device must precede any stream
     capture."""
     B = llr.shape[0]
+    _require("bp_decode_noalloc", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"))
     _check("bp_decode_noalloc", _lib.bp_decode_noalloc(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B,
                                                        _ptr(bits), _ptr(iters), _ptr(crc_ok), _stream(stream)))
 
@@ -359,6 +397,7 @@ class MixedDecoder:
             code, sch, max_iters, llr, slots = part[:5]
             tpf = part[5] if len(part) > 5 else 0
             B = llr.shape[0]
+            _require("bp_mixed_prepare", (llr, torch.float32, (B, code.N), "cuda"))
             bits = torch.empty((B, words_of(code.K)), dtype=torch.int32, device=self.device)
             iters = torch.empty(B, dtype=torch.int32, device=self.device)
             ok = torch.empty(B, dtype=torch.uint8, device=self.device)
@@ -401,14 +440,42 @@ def wbp_workspace_size(code: PcCode, T: int, B: int, real_bytes: int) -> int:
     return out.value
 
 
+def _wbp_checks(fn, code, llr, w, T):
+    """llr [B, N] float32 or float64 CUDA tensor; w the same dtype with wbp_weights_count elements."""
+    import torch
+
+    if llr is None or llr.dtype not in (torch.float32, torch.float64) or llr.dim() != 2:
+        raise PcError(fn, PC_EINVAL)
+    B = llr.shape[0]
+    _require(fn, (llr, llr.dtype, (B, code.N), "cuda"), (w, llr.dtype, tuple(w.shape) if w is not None else (), "cuda"))
+    if w.numel() != wbp_weights_count(code, T):
+        raise PcError(fn, PC_EINVAL)
+    return B
+
+
 def wbp_forward(code: PcCode, llr, w, T: int, logits, ckpt, workspace, stream=None):
     fn = "wbp_forward_f64" if llr.element_size() == 8 else "wbp_forward"
+    B = _wbp_checks(fn, code, llr, w, T)
+    _require(fn, (logits, llr.dtype, (B, code.K), "cuda"))
+    if ckpt is not None:
+        _require(fn, (ckpt, llr.dtype, tuple(ckpt.shape), "cuda"))
+        if ckpt.numel() < wbp_ckpt_count(code, T, B):
+            raise PcError(fn, PC_EINVAL)
+    _require_workspace(fn, workspace, wbp_workspace_size(code, T, B, llr.element_size()))
     _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(logits), _ptr(ckpt),
                                  _ptr(workspace), _stream(stream)))
 
 
 def wbp_backward(code: PcCode, llr, w, T: int, ckpt, glogits, gw, gllr, workspace, stream=None):
     fn = "wbp_backward_f64" if llr.element_size() == 8 else "wbp_backward"
+    B = _wbp_checks(fn, code, llr, w, T)
+    _require(fn, (glogits, llr.dtype, (B, code.K), "cuda"), (gw, llr.dtype, tuple(w.shape), "cuda"),
+             (ckpt, llr.dtype, tuple(ckpt.shape) if ckpt is not None else (), "cuda"))
+    if ckpt.numel() < wbp_ckpt_count(code, T, B):
+        raise PcError(fn, PC_EINVAL)
+    if gllr is not None:
+        _require(fn, (gllr, llr.dtype, (B, code.N), "cuda"))
+    _require_workspace(fn, workspace, wbp_workspace_size(code, T, B, llr.element_size()))
     _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(ckpt), _ptr(glogits),
                                  _ptr(gw), _ptr(gllr), _ptr(workspace), _stream(stream)))
 
@@ -442,8 +509,6 @@ def _wbp_function():
             return gllr, gw, None, None
 
     return WBPFunction
-
-
 
 
 def wbp(llr, w, code: PcCode, T: int):

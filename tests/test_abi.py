@@ -278,3 +278,40 @@ def test_kernel_threads_is_a_host_query(pcbp):
     code = pcbp.pc_construct(256, 128)
     assert pcbp._lib.bp_kernel_threads(C.byref(code), 2, C.byref(out)) == pcbp.PC_EINVAL
     assert pcbp._lib.bp_kernel_threads(C.byref(code), 0, None) == pcbp.PC_EINVAL
+
+
+def test_binding_rejects_tensors_the_calls_cannot_use(pcbp):
+    """The C calls take bare pointers, so the binding checks dtype, shape, contiguity and device
+    first and raises PcError(PC_EINVAL) with nothing enqueued (no GPU needed to see the refusal)."""
+    import torch
+
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    B, KW = 4, pcbp.words_of(128)
+    llr = torch.zeros((B, 256), dtype=torch.float32)
+    bits = torch.zeros((B, KW), dtype=torch.int32)
+    iters = torch.zeros(B, dtype=torch.int32)
+    ok = torch.zeros(B, dtype=torch.uint8)
+    ws = torch.zeros(256, dtype=torch.uint8)
+    s = pcbp.sched()
+    bad = [
+        (llr, bits, iters, ok, ws),                                   # host tensors for a device call
+        (llr.double(), bits, iters, ok, ws),                          # wrong dtype
+        (llr[:, :128], bits, iters, ok, ws),                          # wrong N
+        (torch.zeros((B, 512), dtype=torch.float32)[:, ::2], bits, iters, ok, ws),   # not contiguous
+        (llr, bits[:, :2], iters, ok, ws),                            # too few words per frame
+        (llr, bits, iters[:2], ok, ws),                               # wrong batch
+        (llr, bits, iters, ok.to(torch.int32), ws),                   # wrong flag dtype
+    ]
+    for args in bad:
+        with pytest.raises(pcbp.PcError) as e:
+            pcbp.bp_decode(code, args[0], s, 10, *args[1:])
+        assert e.value.status == pcbp.PC_EINVAL
+    with pytest.raises(pcbp.PcError) as e:                            # host call: layout still checked
+        pcbp.bp_decode_host(code, llr, s, 10, bits, iters[:3], ok, ws)
+    assert e.value.status == pcbp.PC_EINVAL
+    with pytest.raises(pcbp.PcError) as e:
+        pcbp.pc_encode(code, torch.zeros((B, 120), dtype=torch.uint8), torch.zeros((B, 256), dtype=torch.uint8))
+    assert e.value.status == pcbp.PC_EINVAL
+    with pytest.raises(pcbp.PcError) as e:
+        pcbp.wbp_forward(code, llr, torch.zeros(10, dtype=torch.float64), 1, torch.zeros((B, 128)), None, ws)
+    assert e.value.status == pcbp.PC_EINVAL
