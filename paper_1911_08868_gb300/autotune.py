@@ -7,8 +7,7 @@ MixedDecoder, times the launches with CUDA events and keeps the fastest.
 Threads per frame: the counts bp_kernel_threads reports for the two kernels
 (TMEM-resident stage groups: N/4 up to N = 512, N/8 from 1024; shared-memory
 groups: max(32, N/4); where they coincide the library runs the TMEM kernel).  Results are cached per GPU
-name and library in a JSON file ($PCBP_TUNE_CACHE, default
-~/.cache/pcbp_tune.json).
+name and library build in a JSON file ($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
 """
 from __future__ import annotations
 
@@ -56,7 +55,9 @@ def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, e
     from . import inputs, pcbp
 
     dev = torch.device(device)
-    key = f"{torch.cuda.get_device_name(dev)}|{pcbp.library_path()}|{max_iters}|{frames}|{ebn0}|capped"
+    lib = pcbp.library_path()
+    # a rebuilt library (new kernels) is tuned afresh
+    key = f"{torch.cuda.get_device_name(dev)}|{lib}|{os.stat(lib).st_mtime_ns}|{max_iters}|{frames}|{ebn0}|capped"
     cache = {}
     cp = cache_path()
     if use_cache and cp.exists():
