@@ -86,7 +86,7 @@ typedef struct {
     uint64_t frame_base;
 } pc_sched;
 
-/* One explicit permutation event (Algorithm 1, partialPermute).  The
+/* One explicit permutation event (Sec. III, Algorithm 1).  The
  * original factor graph is Arikan's graph of x = u F^{(x)n}: stage l (1..n,
  * counted from the channel) pairs positions that differ in bit n-l.  With
  * m = level+range-1, stages 1..m split the positions into N/2^m subgraphs of

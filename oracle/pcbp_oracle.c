@@ -188,7 +188,7 @@ uint64_t orc_hash(uint64_t seed, uint64_t frame, uint64_t k, uint64_t d)
     return sm64(sm64(sm64(sm64(seed) ^ frame) ^ k) ^ d);
 }
 
-/* Algorithm 1, randomRangeValue / randomLevelValue / partialPermute (Sec. III):
+/* The random choices of a switch (Sec. III, Algorithm 1):
  *   rho_range uniform on {2..P_range} (or fixed),
  *   rho_level = min(x, n - rho_range + 1), x uniform on {1..P_level},
  *   one of the N / 2^(rho_level+rho_range-1) subgraphs uniformly,

@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-/* One partial-permutation event (Algorithm 1, partialPermute): inside the
+/* One partial-permutation event (Sec. III, Algorithm 1): inside the
  * subgraph `block` (indices j with j mod 2^(n-m) == block, m = level+range-1)
  * stage level+i takes the bit that stage level+order[i] has in the original
  * graph.  order is a permutation of 0..range-1. */

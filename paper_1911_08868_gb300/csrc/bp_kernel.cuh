@@ -90,7 +90,7 @@ __device__ __forceinline__ uint64_t event_draw(uint64_t seed, uint64_t frame, ui
     return splitmix_out(splitmix_out(splitmix_out(splitmix_out(seed) ^ frame) ^ k) ^ d);
 }
 
-// randomRangeValue / randomLevelValue / partialPermute (Sec. III); FP-BP
+// The random choices of a switch (Sec. III, Algorithm 1); FP-BP
 // draws a full order (level 1, range n, one block).  The stage order is a
 // uniform non-identity permutation: Fisher-Yates, redrawn while identity, a
 // rotation after 8 identity draws.
@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(1024, 1) bp_decode_kernel(const __grid_constan
                         ctl->next_inc = int(inc);
                     }
                     slot_sync(bar_id, T);
-                    // resetVariableNodes: interior levels of the previous
+                    // the message reset of Sec. III: interior levels of the previous
                     // subgraph (it reverts to the original order) and of the
                     // new one.
                     for (int pass = 0; pass < 2; ++pass) {

@@ -630,7 +630,7 @@ __device__ __forceinline__ void grouped_frames(const FrameJob& J, unsigned long 
                         build_groups<CL, KB>(ctl, s_swz, n, true, level, range, blk, order);
                     }
                     sync();
-                    // resetVariableNodes: R at the interior levels of the previous
+                    // the message reset of Sec. III: R at the interior levels of the previous
                     // subgraph (reverting to the original order) and of the new one
                     for (int pass = 0; pass < 2; ++pass) {
                         if (pass == 0 && !ctl->have_prev) continue;

@@ -1311,7 +1311,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     }
                     fresh = false;
                     sync();
-                    // resetVariableNodes: R at the interior levels of the previous
+                    // the message reset of Sec. III: R at the interior levels of the previous
                     // subgraph (reverting to the original order) and of the new one
                     for (int pass = 0; pass < 2; ++pass) {
                         if (pass == 0 && !ctl->g.have_prev) continue;

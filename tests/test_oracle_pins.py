@@ -114,7 +114,7 @@ def test_eq2_reset_increments_table1(oracle, golden_dir):
 
 
 def test_zeroing_touches_exactly_the_interior_nodes(oracle):
-    """resetVariableNodes after a switch: L and R of the interior levels of the
+    """The message reset of a switch: L and R of the interior levels of the
     chosen subgraph become 0, every other message is unchanged."""
     n, N = 5, 32
     _, fr = oracle.construct(N, 16)
@@ -429,22 +429,29 @@ def test_zero_iterations_decides_all_zero(oracle):
 
 
 def test_fp32_and_fp64_agree_on_noisy_frames(oracle):
-    """FP32 vs FP64 oracle at 3 dB: every frame that either precision decodes
-    correctly gets identical decisions in both; frames that fail may wander
-    apart (rounding steers a non-converging trajectory)."""
+    """FP32 vs FP64 oracle at 3 dB on 20,000 frames: at least 99.9% of the frames
+    that either precision decodes correctly get identical decisions in both
+    (99.8% identical iteration counts),
+    the FERs agree within the binomial 95% interval, and 99% of all frames are
+    identical (frames that fail may wander apart: rounding steers a
+    non-converging trajectory)."""
     N, K, r = 256, 128, 8
     _, fr = oracle.construct(N, K)
-    B = 1500
-    pay = inputs.payload_numpy(21, B, K - r)
+    B = 20000
+    pay = inputs.payload_numpy(22, B, K - r)
     x = oracle.encode_frames(pay, fr, r, POLY8)
-    llr = inputs.bpsk_awgn_llr(x, inputs.noise_numpy(21, B, N), inputs.sigma2_of(3.0, K, r, N))
+    llr = inputs.bpsk_awgn_llr(x, inputs.noise_numpy(22, B, N), inputs.sigma2_of(3.0, K, r, N))
     s = oracle.Sched(mode=1, rho_range_fixed=3, P_level=7, N_min=10, D=0, T0=10, stop_kind=1, seed=3)
     u32, it32, _ = oracle.decode_batch(fr, r, POLY8, llr, s, 50, dtype=np.float32)
     u64, it64, _ = oracle.decode_batch(fr, r, POLY8, llr.astype(np.float64), s, 50, dtype=np.float64)
     same = np.all(u32 == u64, axis=1)
     ok32 = np.all(oracle.info_bits(u32, fr)[:, : K - r] == pay, axis=1)
     ok64 = np.all(oracle.info_bits(u64, fr)[:, : K - r] == pay, axis=1)
-    assert np.all(same[ok32 | ok64])
-    assert np.mean(it32[ok32 | ok64] == it64[ok32 | ok64]) >= 0.99
+    either = ok32 | ok64
+    assert same[either].mean() >= 0.999
+    assert np.mean(it32[either] == it64[either]) >= 0.998     # a marginal frame may pass its CRC one iteration apart
     assert same.mean() >= 0.99
-    assert ok32.mean() > 0.9        # 3 dB, N = 256 rate 1/2: BP decodes the vast majority
+    fer32, fer64 = 1 - ok32.mean(), 1 - ok64.mean()
+    half = 1.96 * np.sqrt(fer64 * (1 - fer64) / B)
+    assert abs(fer32 - fer64) <= half
+    assert 0.01 < fer64 < 0.1        # 3 dB, N = 256 rate 1/2: a few percent of frames fail
