@@ -316,6 +316,12 @@ int bp_decode_mixed(const void* h_table, int32_t n_batches, void* d_workspace, v
  *     contents; each call clears the counter on its stream before decoding.
  *     Calls that overlap on the GPU (other streams, concurrent graph
  *     replays) race on it and must be serialised by the caller.
+ *   Device reset: the looked-up address belongs to the device's context at
+ *     the time of the first call; after cudaDeviceReset it is stale, so do
+ *     not use this entry point again in a process that reset the device.
+ *   Checked build: a PCBP_CHECKED library records kernel range-check failures
+ *     in the workspace's status word; here that word lies in the library's
+ *     array, which callers cannot read, so use bp_decode to see it.
  *   Allocates no device memory (no cudaMalloc or cudaFree). */
 #define PC_STATIC_SCRATCH_BYTES 4096
 int bp_decode_noalloc(const pc_code* code, const float* d_llr, const pc_sched* sched,

@@ -7,7 +7,7 @@ MixedDecoder, times the launches with CUDA events and keeps the fastest.
 Threads per frame: the counts bp_kernel_threads reports for the two kernels
 (TMEM-resident stage groups: N/4 up to N = 512, N/8 from 1024; shared-memory
 groups: max(32, N/4); where they coincide the library runs the TMEM kernel).  Results are cached per GPU
-name and library build in a JSON file ($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
+name, library build and schedule in a JSON file ($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
 """
 from __future__ import annotations
 
@@ -16,6 +16,9 @@ import os
 from pathlib import Path
 
 SLOT_CANDIDATES = (1, 2, 3, 4, 6, 8, 12, 16, 24)
+# pc_sched fields that select the kernel variant or change the work per frame
+SCHED_KEY_FIELDS = ("fkind", "mode", "stop_kind", "stop_from", "rho_range_fixed", "P_range", "P_level", "T0",
+                    "N_min", "D", "q_max", "it_reset_full", "alpha")
 
 
 def cache_path() -> Path:
@@ -68,13 +71,15 @@ def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, e
     entry = cache.get(key, {})
     best = {}
     for N in lengths:
-        if str(N) in entry and isinstance(entry[str(N)], dict):
-            best[N] = dict(entry[str(N)])
+        sch = sched_for(N.bit_length() - 1)
+        # the kernel variant (f, stop test) and the work per frame depend on the schedule
+        skey = f"{N}|" + "|".join(f"{getattr(sch, f)}" for f in SCHED_KEY_FIELDS)
+        if skey in entry and isinstance(entry[skey], dict):
+            best[N] = dict(entry[skey])
             continue
         K = N // 2
         r, poly = crc_for(N)
         code, llr = _synthetic(pcbp, inputs, dev, N, K, r, poly, frames, ebn0, seed=N)
-        sch = sched_for(N.bit_length() - 1)
         times = {}
         for tpf in threads_candidates(pcbp, code):
             limit = pcbp.bp_slot_limit(code, tpf, int(sch.fkind))
@@ -92,7 +97,7 @@ def tune_launch(lengths, sched_for, max_iters: int = 300, frames: int = 16384, e
                 times[(tpf, slots)] = t0.elapsed_time(t1) / reps
         tpf, slots = min(times, key=lambda c: (round(times[c], 3), c[1]))
         best[N] = {"threads_per_frame": tpf, "slots": slots, "ms": times[(tpf, slots)]}
-        entry[str(N)] = best[N]
+        entry[skey] = best[N]
     if use_cache:
         cache[key] = entry
         try:

@@ -14,7 +14,11 @@
 // that device; that first call therefore has to come before any stream
 // capture.  Every call shares the array and its contents persist between
 // calls: the decoder clears the counter on the stream at the start of each
-// call, and calls that overlap on the GPU race on it.
+// call, and calls that overlap on the GPU race on it.  The cached address is
+// that of the device's context at the first call; after cudaDeviceReset it is
+// stale, so a process that resets a device must not call this entry point on
+// it again.  In a PCBP_CHECKED build the range-check status word also lands in
+// the array, where callers cannot read it (bp_decode reports it).
 #include <cuda_runtime.h>
 
 #include <mutex>

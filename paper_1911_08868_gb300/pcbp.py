@@ -104,19 +104,41 @@ def _ptr(t):
     return None if t is None else C.c_void_p(t.data_ptr())
 
 
+def _on_current_device(t) -> bool:
+    """The C calls launch on the calling thread's current device and hand it the pointers as they
+    are, so a device tensor must live on that device (another GPU's memory would be dereferenced
+    by the wrong device)."""
+    import torch
+
+    return t.device == torch.device("cuda", torch.cuda.current_device())
+
+
 def _require(fn: str, *checks):
     """Raise PcError(PC_EINVAL) unless every (tensor, dtype, shape, where) check holds: the C calls
     receive bare pointers, so the tensors behind them must have the layout the call assumes.
-    where: "cuda" (device memory), "any" (device or host; the call checks host memory itself)."""
+    where: "cuda" (memory of the current device), "any" (host memory, which the call checks
+    itself, or memory of the current device)."""
     for t, dtype, shape, where in checks:
         ok = (t is not None and t.dtype == dtype and tuple(t.shape) == tuple(shape) and t.is_contiguous()
-              and (where != "cuda" or t.is_cuda))
+              and (where != "cuda" or t.is_cuda) and (not t.is_cuda or _on_current_device(t)))
         if not ok:
             raise PcError(fn, PC_EINVAL)
 
 
 def _require_workspace(fn: str, ws, nbytes: int, where: str = "cuda"):
-    if ws is None or not ws.is_contiguous() or ws.numel() * ws.element_size() < nbytes or (where == "cuda" and not ws.is_cuda):
+    if (ws is None or not ws.is_contiguous() or ws.numel() * ws.element_size() < nbytes
+            or (where == "cuda" and not ws.is_cuda) or (ws.is_cuda and not _on_current_device(ws))):
+        raise PcError(fn, PC_EINVAL)
+
+
+def _require_stream(fn: str, stream):
+    """A stream object passed in must belong to the current device (raw handles are passed through)."""
+    if stream is None or isinstance(stream, int):
+        return
+    import torch
+
+    dev = getattr(stream, "device", None)
+    if dev is not None and torch.device(dev) != torch.device("cuda", torch.cuda.current_device()):
         raise PcError(fn, PC_EINVAL)
 
 
@@ -175,6 +197,7 @@ def pc_encode(code: PcCode, payload, x_out, stream=None):
     B = x_out.shape[0]
     _require("pc_encode", (payload, torch.uint8, (B, code.K - code.crc_len), "cuda"),
              (x_out, torch.uint8, (B, code.N), "cuda"))
+    _require_stream("pc_encode", stream)
     _check("pc_encode", _lib.pc_encode(C.byref(code), _ptr(payload), _ptr(x_out), B, _stream(stream)))
 
 
@@ -189,6 +212,7 @@ def bp_decode(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_
     B = llr.shape[0]
     _require("bp_decode", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"))
     _require_workspace("bp_decode", workspace, bp_decode_workspace_size(code, B))
+    _require_stream("bp_decode", stream)
     _check("bp_decode", _lib.bp_decode(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
                                        _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
 
@@ -199,6 +223,7 @@ def bp_decode_host(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters,
     B = llr.shape[0]
     _require("bp_decode_host", *_decode_checks(code, llr, bits, iters, crc_ok, "any"))
     _require_workspace("bp_decode_host", workspace, bp_decode_workspace_size(code, B))
+    _require_stream("bp_decode_host", stream)
     _check("bp_decode_host", _lib.bp_decode_host(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, _ptr(bits),
                                                  _ptr(iters), _ptr(crc_ok), _ptr(workspace), _stream(stream)))
 
@@ -219,6 +244,7 @@ def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dum
     else:
         arr = (PcEvent * max(len(events), 1))(*events)
         evp, nev = arr, len(events)
+    _require_stream("bp_decode_trace", stream)
     _check("bp_decode_trace", _lib.bp_decode_trace(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, evp, nev,
                                                    _ptr(dump), _ptr(bits), _ptr(iters), _ptr(crc_ok),
                                                    _ptr(workspace), _stream(stream)))
@@ -231,6 +257,7 @@ def bp_decode_noalloc(code: PcCode, llr, sch: PcSched, max_iters: int, bits, ite
     capture."""
     B = llr.shape[0]
     _require("bp_decode_noalloc", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"))
+    _require_stream("bp_decode_noalloc", stream)
     _check("bp_decode_noalloc", _lib.bp_decode_noalloc(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B,
                                                        _ptr(bits), _ptr(iters), _ptr(crc_ok), _stream(stream)))
 
@@ -260,9 +287,12 @@ class Decoder:
             self._B = B
 
     def __call__(self, llr, stream=None):
+        import torch
+
         self._ensure(llr.shape[0])
-        bp_decode(self.code, llr, self.sched, self.max_iters, self.bits, self.iters, self.crc_ok, self.workspace,
-                  stream)
+        with torch.cuda.device(self.device):
+            bp_decode(self.code, llr, self.sched, self.max_iters, self.bits, self.iters, self.crc_ok,
+                      self.workspace, stream)
         return self.bits, self.iters, self.crc_ok
 
 
@@ -312,8 +342,9 @@ class HostDecoder:
         self._ensure(h_llr.shape[0])
         # work the caller queued on its current stream (e.g. an asynchronous fill of h_llr) comes first
         self.stream.wait_stream(torch.cuda.current_stream(self.device))
-        bp_decode_host(self.code, h_llr, self.sched, self.max_iters, self.h_bits, self.h_iters, self.h_ok,
-                       self.workspace, self.stream)
+        with torch.cuda.device(self.device):
+            bp_decode_host(self.code, h_llr, self.sched, self.max_iters, self.h_bits, self.h_iters, self.h_ok,
+                           self.workspace, self.stream)
         self.stream.synchronize()
         return self.h_bits, self.h_iters, self.h_ok
 
@@ -373,6 +404,7 @@ def bp_mixed_prepare(batches, h_table):
 
 
 def bp_decode_mixed(h_table, n_batches, workspace, stream=None):
+    _require_stream("bp_decode_mixed", stream)
     _check("bp_decode_mixed", _lib.bp_decode_mixed(C.cast(h_table, C.c_void_p), n_batches, _ptr(workspace),
                                                    _stream(stream)))
 
@@ -462,6 +494,7 @@ def wbp_forward(code: PcCode, llr, w, T: int, logits, ckpt, workspace, stream=No
         if ckpt.numel() < wbp_ckpt_count(code, T, B):
             raise PcError(fn, PC_EINVAL)
     _require_workspace(fn, workspace, wbp_workspace_size(code, T, B, llr.element_size()))
+    _require_stream(fn, stream)
     _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(logits), _ptr(ckpt),
                                  _ptr(workspace), _stream(stream)))
 
@@ -476,6 +509,7 @@ def wbp_backward(code: PcCode, llr, w, T: int, ckpt, glogits, gw, gllr, workspac
     if gllr is not None:
         _require(fn, (gllr, llr.dtype, (B, code.N), "cuda"))
     _require_workspace(fn, workspace, wbp_workspace_size(code, T, B, llr.element_size()))
+    _require_stream(fn, stream)
     _check(fn, getattr(_lib, fn)(C.byref(code), _ptr(llr), _ptr(w), T, llr.shape[0], _ptr(ckpt), _ptr(glogits),
                                  _ptr(gw), _ptr(gllr), _ptr(workspace), _stream(stream)))
 

@@ -315,3 +315,85 @@ def test_binding_rejects_tensors_the_calls_cannot_use(pcbp):
     with pytest.raises(pcbp.PcError) as e:
         pcbp.wbp_forward(code, llr, torch.zeros(10, dtype=torch.float64), 1, torch.zeros((B, 128)), None, ws)
     assert e.value.status == pcbp.PC_EINVAL
+
+
+class _FakeDeviceTensor:
+    """Stands in for a contiguous CUDA tensor on a given device, so that the binding's device check
+    can be exercised without a GPU."""
+
+    def __init__(self, shape, dtype, index):
+        import torch
+
+        self.shape, self.dtype = tuple(shape), dtype
+        self.device = torch.device("cuda", index)
+        self.is_cuda = True
+
+    def is_contiguous(self):
+        return True
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        out = 1
+        for d in self.shape:
+            out *= d
+        return out
+
+    def element_size(self):
+        return self.dtype.itemsize
+
+    def data_ptr(self):
+        raise AssertionError("the binding took a pointer of a tensor it should have refused")
+
+
+class _NoCalls:
+    def __getattr__(self, name):
+        if name == "pc_status_string":
+            import ctypes
+
+            return lambda status: ctypes.c_char_p(b"invalid argument").value
+        raise AssertionError(f"C call {name} reached although the arguments were refused")
+
+
+def test_binding_rejects_tensors_of_another_device(pcbp, monkeypatch):
+    """The C calls launch on the current device: tensors (or a stream) of another GPU are refused
+    with PcError(PC_EINVAL) before any C call."""
+    import torch
+
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    ws_bytes = pcbp.bp_decode_workspace_size(code, 4)
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(pcbp, "bp_decode_workspace_size", lambda code, B: ws_bytes)
+    monkeypatch.setattr(pcbp, "_lib", _NoCalls())
+    B, KW = 4, pcbp.words_of(128)
+
+    def args(dev_llr=0, dev_ws=0, dev_out=0):
+        return (_FakeDeviceTensor((B, 256), torch.float32, dev_llr), _FakeDeviceTensor((B, KW), torch.int32, dev_out),
+                _FakeDeviceTensor((B,), torch.int32, dev_out), _FakeDeviceTensor((B,), torch.uint8, dev_out),
+                _FakeDeviceTensor((ws_bytes,), torch.uint8, dev_ws))
+
+    s = pcbp.sched()
+    for kw in ({"dev_llr": 1}, {"dev_ws": 1}, {"dev_out": 1}):
+        llr, bits, iters, ok, ws = args(**kw)
+        calls = [lambda: pcbp.bp_decode(code, llr, s, 10, bits, iters, ok, ws),
+                 lambda: pcbp.bp_decode_host(code, llr, s, 10, bits, iters, ok, ws)]
+        if "dev_ws" not in kw:      # bp_decode_noalloc takes no workspace
+            calls.append(lambda: pcbp.bp_decode_noalloc(code, llr, s, 10, bits, iters, ok))
+        for call in calls:
+            with pytest.raises(pcbp.PcError) as e:
+                call()
+            assert e.value.status == pcbp.PC_EINVAL, kw
+
+    class _Stream:
+        device = torch.device("cuda", 1)
+        cuda_stream = 0
+
+    llr, bits, iters, ok, ws = args()
+    for call in (lambda: pcbp.bp_decode(code, llr, s, 10, bits, iters, ok, ws, _Stream()),
+                 lambda: pcbp.bp_decode_noalloc(code, llr, s, 10, bits, iters, ok, _Stream()),
+                 lambda: pcbp.pc_encode(code, _FakeDeviceTensor((B, 120), torch.uint8, 0),
+                                        _FakeDeviceTensor((B, 256), torch.uint8, 0), _Stream())):
+        with pytest.raises(pcbp.PcError) as e:
+            call()
+        assert e.value.status == pcbp.PC_EINVAL
