@@ -9,6 +9,10 @@ LLRs (4.1 GB per step) are resident in HBM and larger than L2.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+With --gpus N > 1 and no torchrun environment, bench.py re-launches itself
+as N local ranks under torch.distributed.run (one per GPU, frames sharded,
+weak scaling).
+
 Prints one JSON line.  `value` is decoded information (payload) Gbit/s over
 all ranks, timed with CUDA events around the decoder launches; `e2e` is the
 same metric through the host-buffer API (bp_decode_host: the decoder reads
@@ -70,6 +74,27 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def free_port() -> int:
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def spawn_ranks(nproc: int, script: str, argv) -> int:
+    """Runs `script argv` as nproc local ranks under torch.distributed.run (one process per GPU,
+    rendezvous on 127.0.0.1) and returns its exit status; rank 0 prints the JSON line."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={nproc}",
+           "--master-addr", "127.0.0.1", f"--master-port={free_port()}", script, *argv]
+    return subprocess.run(cmd).returncode
+
+
+def needs_spawn(gpus: int) -> bool:
+    """--gpus N > 1 outside torchrun: bench.py launches its own N ranks."""
+    return gpus > 1 and "WORLD_SIZE" not in os.environ
 
 
 def kernel_sha() -> str:
@@ -757,6 +782,8 @@ def run_ours(args):
 
 def main():
     args = parse()
+    if needs_spawn(args.gpus) and not args.sweep:
+        sys.exit(spawn_ranks(args.gpus, str(Path(__file__).resolve()), sys.argv[1:]))
     if args.sweep:
         run_sweep(args)
     elif args.impl == "reference":
