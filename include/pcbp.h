@@ -178,6 +178,29 @@ int bp_decode_trace(const pc_code* code, const float* d_llr, const pc_sched* sch
                     int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace,
                     void* stream);
 
+/* bp_decode (Algorithm 1) through the same production kernel, which also
+ * records the messages at both ends of the factor graph after each frame's
+ * last iteration, for verification of the message arithmetic (Sec. II-B)
+ * where the outputs alone would hide it (the exact box-plus f).
+ *   d_post: B x 2 x N floats, device memory, 4-byte aligned; block [b][0]
+ *     receives L at node level n+1 (the u side), block [b][1] R at node
+ *     level 1 (the channel side), both after frame b's last iteration, whose
+ *     R sweep is always completed.  Left untouched when max_iters is 0.
+ *   Other arguments and outputs as bp_decode (the outputs are equal).
+ * Returns PC_EUNSUPPORTED for N < 128 (those lengths run another kernel) or
+ * with the G-matrix stop test (stop_kind & 2). */
+int bp_decode_posterior(const pc_code* code, const float* d_llr, const pc_sched* sched,
+                        int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
+                        uint8_t* d_crc_ok, float* d_post, void* d_workspace, void* stream);
+
+/* The processing-element function f of Sec. II-B, elementwise, exactly as
+ * the decoder kernels evaluate it, for verification of its arithmetic:
+ * d_out[i] = f(d_a[i], d_b[i]) with fkind 0 (scaled min-sum, alpha) or 1
+ * (exact box-plus, alpha unused).  Device arrays of count floats, 4-byte
+ * aligned; asynchronous on stream. */
+int pc_f_eval(const float* d_a, const float* d_b, float* d_out, int64_t count,
+              int32_t fkind, float alpha, void* stream);
+
 /* ---- Weighted BP (a differentiable variant; the paper has no counterpart) -
  * Unrolled round-trip BP on the original factor graph (Sec. II-B) with a
  * learnable scale per f evaluation in place of the fixed min-sum scale:

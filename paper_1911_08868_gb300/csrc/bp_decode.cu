@@ -145,6 +145,17 @@ int occupancy3_of(int n, const LaunchGeom& g, int fk)
     }
 }
 
+cudaError_t launch3_post_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st)
+{
+    switch (n) {
+        case 7: return bp3_launch_post_7(P, g, fk, st);
+        case 8: return bp3_launch_post_8(P, g, fk, st);
+        case 9: return bp3_launch_post_9(P, g, fk, st);
+        case 10: return bp3_launch_post_10(P, g, fk, st);
+        default: return bp3_launch_post_11(P, g, fk, st);
+    }
+}
+
 cudaError_t launch3_of(int n, const BpParams& P, const LaunchGeom& g, int fk, cudaStream_t st, bool pdl)
 {
     switch (n) {
@@ -324,9 +335,11 @@ void fill_params(const pc_code* code, const float* d_llr, const pc_sched* sched,
     P->job.r = code->crc_len;
 }
 
+// d_post (posterior output, nullable): the TMEM kernel's debug build that also writes L at node
+// level n+1 and R at node level 1 of every frame's last iteration.
 int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched, int32_t max_iters, int64_t B,
                   bool trace, const pc_event* h_events, int32_t n_events, float* d_dump, uint32_t* d_bits,
-                  int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace, void* stream)
+                  int32_t* d_iters, uint8_t* d_crc_ok, void* d_workspace, void* stream, float* d_post = nullptr)
 {
     int rc = validate_code(code);
     if (rc != PC_OK) return rc;
@@ -337,6 +350,10 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     if (!d_llr || !d_bits || !d_iters || !d_crc_ok || !d_workspace) return PC_EINVAL;
     if ((reinterpret_cast<uintptr_t>(d_llr) & 15u) || (reinterpret_cast<uintptr_t>(d_workspace) & 255u))
         return PC_EINVAL;
+    if (d_post) {
+        if (trace || code->n < 7 || code->n > 11 || (sched->stop_kind & 2)) return PC_EUNSUPPORTED;
+        if (reinterpret_cast<uintptr_t>(d_post) & 3u) return PC_EINVAL;
+    }
     if (trace) {
         if (!d_dump) return PC_EINVAL;
         if (h_events) {
@@ -359,8 +376,10 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
     P->counter = reinterpret_cast<unsigned long long*>(d_workspace);
     P->dump = d_dump;
 
+    P->job.post = d_post;
+
     LaunchGeom g;
-    const bool tmem = !trace && use_tmem_kernel(code->n);
+    const bool tmem = !trace && (d_post || use_tmem_kernel(code->n));
     rc = trace ? plan_launch(code, B, trace, sched->fkind, &g)
                : (tmem ? plan_launch3(code, B, sched->fkind, &g) : plan_launch2(code, B, sched->fkind, &g));
     if (rc != PC_OK) return rc;
@@ -373,9 +392,10 @@ int decode_common(const pc_code* code, const float* d_llr, const pc_sched* sched
 #else
     if (cudaMemsetAsync(d_workspace, 0, sizeof(unsigned long long), st) != cudaSuccess) return PC_ECUDA;
 #endif
-    const cudaError_t e = trace  ? launch_of(code->n, *P, g, true, sched->fkind, st)
-                          : tmem ? launch3_of(code->n, *P, g, sched->fkind, st, false)
-                                 : launch2_of(code->n, *P, g, sched->fkind, st, false);
+    const cudaError_t e = trace    ? launch_of(code->n, *P, g, true, sched->fkind, st)
+                          : d_post ? launch3_post_of(code->n, *P, g, sched->fkind, st)
+                          : tmem   ? launch3_of(code->n, *P, g, sched->fkind, st, false)
+                                   : launch2_of(code->n, *P, g, sched->fkind, st, false);
     if (e != cudaSuccess) return PC_ECUDA;
     return PC_OK;
 }
@@ -459,6 +479,15 @@ extern "C" int bp_decode(const pc_code* code, const float* d_llr, const pc_sched
 {
     return decode_common(code, d_llr, sched, max_iters, B, false, nullptr, 0, nullptr, d_bits, d_iters, d_crc_ok,
                          d_workspace, stream);
+}
+
+extern "C" int bp_decode_posterior(const pc_code* code, const float* d_llr, const pc_sched* sched,
+                                   int32_t max_iters, int64_t B, uint32_t* d_bits, int32_t* d_iters,
+                                   uint8_t* d_crc_ok, float* d_post, void* d_workspace, void* stream)
+{
+    if (B > 0 && !d_post) return PC_EINVAL;
+    return decode_common(code, d_llr, sched, max_iters, B, false, nullptr, 0, nullptr, d_bits, d_iters, d_crc_ok,
+                         d_workspace, stream, B > 0 ? d_post : nullptr);
 }
 
 // ---------------------------------------------------------------------------

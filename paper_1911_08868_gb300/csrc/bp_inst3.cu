@@ -22,10 +22,10 @@ using Geo = G3<PCBP_LOGN, KB>;
 
 // pdl: programmatic dependent launch, the grid may start while the previous
 // kernel of the stream still runs (for independent batches).
-template <int FK, int WG>
+template <int FK, int WG, int PO = 0>
 cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t st, bool pdl)
 {
-    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, WG>;
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, WG, PO>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));
     if (e != cudaSuccess) return e;
     if (!pdl) {
@@ -48,7 +48,7 @@ cudaError_t launch_variant(const BpParams& P, const LaunchGeom& g, cudaStream_t 
 template <int FK>
 int occupancy(const LaunchGeom& g)
 {
-    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, 0>;
+    auto kern = bp_decode_tmem_kernel<PCBP_LOGN, KB, FK, 0, 0>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) != cudaSuccess)
         return 0;
     int blocks = 0;
@@ -84,6 +84,13 @@ cudaError_t PCBP_CAT(bp3_launch_, PCBP_LOGN)(const BpParams& P, const LaunchGeom
     const bool wg = (P.job.S.stop_kind & 2) != 0;
     if (fkind) return wg ? launch_variant<1, 1>(P, g, st, pdl) : launch_variant<1, 0>(P, g, st, pdl);
     return wg ? launch_variant<0, 1>(P, g, st, pdl) : launch_variant<0, 0>(P, g, st, pdl);
+}
+
+// The same kernel with the posterior output (CRC stop or none; P.job.post set).
+cudaError_t PCBP_CAT(bp3_launch_post_, PCBP_LOGN)(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st)
+{
+    if (P.job.S.stop_kind & 2) return cudaErrorInvalidValue;
+    return fkind ? launch_variant<1, 0, 1>(P, g, st, false) : launch_variant<0, 0, 1>(P, g, st, false);
 }
 
 }  // namespace pcbp

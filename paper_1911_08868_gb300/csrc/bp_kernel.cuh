@@ -142,15 +142,50 @@ __device__ __forceinline__ float fnode<0>(float a, float b, float alpha)
     return __fmul_rn(alpha, m);
 }
 
+// Hardware base-2 exponential and reciprocal (approximate, subnormals flushed).
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Exact box-plus: f(a, b) = sign(a) sign(b) min(|a|, |b|) + c with the
+// correction c = log1p(e^-|a+b|) - log1p(e^-|a-b|).  With p = e^-|a+b| and
+// q = e^-|a-b|, both in [0, 1],
+//   c = ln((1 + p) / (1 + q)) = 2 atanh(s),   s = (p - q) / (2 + p + q),  |s| <= 1/3,
+// and 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + ...) is summed through s^13/13 in
+// Horner form in s^2; the omitted tail is at most (1/3)^15 / 15 / (1 - 1/9),
+// below 5.2e-9.  p and q come from the hardware base-2 exponential
+// (e^-t = 2^(-t log2 e)), s from the hardware reciprocal.  One infinite
+// operand gives p = q = 0, so c = 0 and f is the other operand's value with
+// the product sign; two infinite operands return the min term directly.
 template <>
 __device__ __forceinline__ float fnode<1>(float a, float b, float)
 {
+    constexpr float kNegLog2e = -1.44269504088896341f;
     float sm;
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(sm) : "f"(a), "f"(b));
-    if (isinf(a) || isinf(b)) return sm;
-    const float c1 = log1pf(expf(-fabsf(__fadd_rn(a, b))));
-    const float c2 = log1pf(expf(-fabsf(__fsub_rn(a, b))));
-    return __fsub_rn(__fadd_rn(sm, c1), c2);
+    const float p = ex2_approx(__fmul_rn(fabsf(__fadd_rn(a, b)), kNegLog2e));
+    const float q = ex2_approx(__fmul_rn(fabsf(__fsub_rn(a, b)), kNegLog2e));
+    const float s = __fmul_rn(__fsub_rn(p, q), rcp_approx(__fadd_rn(2.f, __fadd_rn(p, q))));
+    const float z = __fmul_rn(s, s);
+    float h = 1.f / 13.f;
+    h = __fmaf_rn(h, z, 1.f / 11.f);
+    h = __fmaf_rn(h, z, 1.f / 9.f);
+    h = __fmaf_rn(h, z, 1.f / 7.f);
+    h = __fmaf_rn(h, z, 1.f / 5.f);
+    h = __fmaf_rn(h, z, 1.f / 3.f);
+    h = __fmaf_rn(h, z, 1.f);
+    const float v = __fmaf_rn(__fmul_rn(2.f, s), h, sm);
+    return isinf(sm) ? sm : v;
 }
 
 __device__ __forceinline__ float prior_of(const uint32_t* frozen, int j)

@@ -640,11 +640,14 @@ __device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S,
 
 // One permuted stage s narrower than a register group (m < KB events), with
 // per-PE addressing: the L sweep (r_sweep false) or the R sweep of stage s.
+// The R sweep of stage 0 sets the hard-decision bits of L + R at node level 1
+// in xh, or, when post1 is given, writes R at node level 1 there instead.
 // E/2 PEs per thread; out of line (rare).
 template <int LOGN, int E, int T, int FK>
 __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowmask, int beta, int lo, int m1, int pbit,
                                           const float* llr_f, float* Lp, float* Rp, uint32_t* xh,
-                                          const unsigned char* s_swz, float alpha, unsigned* check)
+                                          const unsigned char* s_swz, float alpha, unsigned* check,
+                                          float* post1 = nullptr)
 {
     constexpr int n = LOGN;
     constexpr int N = 1 << LOGN;
@@ -677,6 +680,9 @@ __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowm
             if (s >= 1) {
                 Rp[(s - 1) * N + sw(t)] = o1;
                 Rp[(s - 1) * N + sw(b)] = o2;
+            } else if (post1) {
+                post1[t] = o1;
+                post1[b] = o2;
             } else {
                 if (__fadd_rn(lt, o1) < 0.f) atomicOr(&xh[t >> 5], 1u << (t & 31));
                 if (__fadd_rn(lb, o2) < 0.f) atomicOr(&xh[b >> 5], 1u << (b & 31));
@@ -718,7 +724,10 @@ __device__ __noinline__ void build_template(Ctl3<LOGN, KB>* c, const unsigned ch
     pack_groups<LOGN, KB>(c);
 }
 
-template <int LOGN, int KB, int FK, int WG>
+// PO = 1 (posterior output, a debug build of the same sweeps): every frame
+// also writes L at node level n+1 and R at node level 1 after its last
+// iteration to J.post, and that iteration always completes its R sweep.
+template <int LOGN, int KB, int FK, int WG, int PO>
 __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long long* counter, unsigned char* smem,
                                             uint32_t tm_base)
 {
@@ -805,6 +814,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int KW = (K + 31) / 32;
     const int max_iters = J.max_iters;
     constexpr bool want_g = WG != 0;     // the G-matrix test is on (stop_kind & 2), fixed per launch
+    static_assert(!(PO && WG), "the posterior output is built for the CRC stop only");
     const bool want_crc = (S.stop_kind & 1) != 0;
 
     float L1[E];   // channel LLRs of the first group's positions
@@ -1083,6 +1093,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     for (int e = 0; e < E; ++e) xL[i][e] = x[e];
                     l_layer<E, FK>(x, i < GLL - 1 ? rp[i < GLL - 1 ? i : 0] : pr, i, alpha);
                 }
+                if constexpr (PO != 0) {
+                    // L at node level n+1, overwritten every iteration (the barriers between
+                    // iterations order the writes of different threads)
+                    float* po = J.post + size_t(f) * 2 * N;
+#pragma unroll
+                    for (int e = 0; e < E; ++e) po[pos_of(AL[e], s0L)] = x[e];
+                }
                 // a5: decisions u_j = [L(n+1) + R(n+1) < 0], taken as L(n+1) < -R(n+1) (a
                 // rounded sum has the sign of the exact one), and their CRC residue
                 unsigned part = 0;
@@ -1143,6 +1160,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             // next barrier of this kind comes before anyone accumulates iteration it+2
             if (tid == 0) ctl->crc_part[pb == 0 ? 2 : pb - 1] = 0u;
 
+            bool po_end = false;     // PO: the frame's last iteration, finished after its R sweep
             if (!want_g) {
                 const bool stop = check && res == 0u;
                 if (stop || it == max_iters) {
@@ -1172,7 +1190,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     }
                     sync();
                     if (stop) used = it;
-                    break;
+                    if constexpr (PO == 0) break;
+                    po_end = true;
                 }
             }
 
@@ -1183,10 +1202,11 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 const int4 rc = ctl->rec[gi];
                 const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
                 if (SINGLES && ((rc.x >> 16) & 1)) {
-                    if (!FIRST || want_g)
+                    if (!FIRST || want_g || PO)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                      ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
-                                                     Rp, xh, s_swz, alpha, J.check);
+                                                     Rp, xh, s_swz, alpha, J.check,
+                                                     (PO && FIRST) ? J.post + size_t(f) * 2 * N + N : nullptr);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
@@ -1210,13 +1230,17 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         }
 #pragma unroll
                         for (int i = GL - 1; i >= 0; --i) {
-                            if (FIRST && i == 0 && !want_g) continue;      // stage 0 writes only the G-matrix bits
+                            if (FIRST && i == 0 && !want_g && !PO) continue;      // stage 0 writes only the G-matrix bits
                             r_layer<E, FK>(y, lv[i], i, alpha);
                             if (i > 0) {
                                 tm_st<E>(tc(colL + uint32_t((GL + i - 1) * E)), y);            // R level s0+1+i
                             } else if (!FIRST) {
 #pragma unroll
                                 for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
+                            } else if (PO) {
+                                float* po = J.post + size_t(f) * 2 * N + N;      // R at node level 1
+#pragma unroll
+                                for (int e = 0; e < E; ++e) po[pos_of(A[e], 0)] = y[e];
                             } else if (!((rc.x >> 24) & 1) && int((signed char)(rc.z & 0xff)) == n - KB) {
                                 // the register bits are the top KB position bits (every thread in
                                 // class 0), so the lanes are position bits 0..4: per register, one
@@ -1265,6 +1289,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 #pragma unroll 1
                 for (int gi = ng - 2; gi >= 1; --gi) r_group(gi, std::false_type{}, std::true_type{});
                 r_group(0, std::true_type{}, std::true_type{});
+            }
+            if constexpr (PO != 0) {
+                if (po_end) {
+                    sync();
+                    break;
+                }
             }
 
             if (want_g) {
@@ -1375,7 +1405,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     tm_wait_st();
 }
 
-template <int LOGN, int KB, int FK, int WG>
+template <int LOGN, int KB, int FK, int WG, int PO>
 __global__ void __launch_bounds__(tmem_max_threads<LOGN, KB>(), 1) bp_decode_tmem_kernel(const __grid_constant__ BpParams P)
 {
     // a kernel launched after this one may start as soon as SMs free up
@@ -1399,7 +1429,7 @@ __global__ void __launch_bounds__(tmem_max_threads<LOGN, KB>(), 1) bp_decode_tme
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm_base = s_tm;
-    if (int(threadIdx.x) < P.slots * G3<LOGN, KB>::T) tmem_frames<LOGN, KB, FK, WG>(P.job, P.counter, smem, tm_base);
+    if (int(threadIdx.x) < P.slots * G3<LOGN, KB>::T) tmem_frames<LOGN, KB, FK, WG, PO>(P.job, P.counter, smem, tm_base);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

@@ -41,7 +41,8 @@ PCBP_DECLARE_LEN(11)
     void bp3_shape_##n(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out); \
     void bp3_tables_##n(int N, int K, size_t* bytes);                                          \
     int bp3_occupancy_##n(const LaunchGeom& g, int fkind);                                     \
-    cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st, bool pdl);
+    cudaError_t bp3_launch_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st, bool pdl); \
+    cudaError_t bp3_launch_post_##n(const BpParams& P, const LaunchGeom& g, int fkind, cudaStream_t st);
 
 PCBP_DECLARE_LEN3(7)
 PCBP_DECLARE_LEN3(8)

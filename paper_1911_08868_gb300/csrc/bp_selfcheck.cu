@@ -1,11 +1,13 @@
-// Internal consistency check of the TMEM kernel's two partition builders
-// (no counterpart in the paper): for every event shape of N = 128..2048 and
+// Verification entry points (no counterpart in the paper).  Internal
+// consistency check of the TMEM kernel's two partition builders: for every event shape of N = 128..2048 and
 // three orders and blocks each, the warp-parallel builder used at a switch
 // must produce the packed records that build_groups + pack_groups produce,
 // and every partition (the no-event one included) must have the shape the
 // kernel's sweeps assume: at least two groups, and every group other than the
 // first and the last either a single stage or a full KB stages.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "bp_kernel3.cuh"
 
@@ -89,5 +91,42 @@ extern "C" int pc_partition_selfcheck(int32_t* d_result, void* stream)
     partition_selfcheck_kernel<9, tmem_default_kb(9)><<<1, 32, 0, st>>>(d_result);
     partition_selfcheck_kernel<10, tmem_default_kb(10)><<<1, 32, 0, st>>>(d_result);
     partition_selfcheck_kernel<11, tmem_default_kb(11)><<<1, 32, 0, st>>>(d_result);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
+// The processing-element function f of Sec. II-B exactly as the decoder
+// kernels evaluate it, elementwise (for checking its arithmetic).
+namespace pcbp {
+namespace {
+
+template <int FK>
+__global__ void f_eval_kernel(const float* __restrict__ a, const float* __restrict__ b, float* __restrict__ out,
+                              int64_t count, float alpha)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < count; i += int64_t(gridDim.x) * blockDim.x)
+        out[i] = fnode<FK>(a[i], b[i], alpha);
+}
+
+}  // namespace
+}  // namespace pcbp
+
+extern "C" int pc_f_eval(const float* d_a, const float* d_b, float* d_out, int64_t count, int32_t fkind, float alpha,
+                         void* stream)
+{
+    if (count < 0 || (fkind != 0 && fkind != 1)) return PC_EINVAL;
+    if (count == 0) return PC_OK;
+    if (!d_a || !d_b || !d_out) return PC_EINVAL;
+    if ((reinterpret_cast<uintptr_t>(d_a) | reinterpret_cast<uintptr_t>(d_b) | reinterpret_cast<uintptr_t>(d_out)) &
+        3u)
+        return PC_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PC_ECUDA;
+    const int grid = int(std::min<int64_t>((count + 255) / 256, int64_t(sms) * 8));
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (fkind) f_eval_kernel<1><<<grid, 256, 0, st>>>(d_a, d_b, d_out, count, alpha);
+    else f_eval_kernel<0><<<grid, 256, 0, st>>>(d_a, d_b, d_out, count, alpha);
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
 }

@@ -50,6 +50,7 @@ struct FrameJob {
     int32_t max_iters;
     int32_t K, r;
     unsigned* check;   // builds with PCBP_CHECKED: bit c set when an access of class c was out of range (nullable)
+    float* post;       // posterior-output kernels only: [B][2][N], L at node level n+1, R at node level 1
 };
 
 struct DevEvent {

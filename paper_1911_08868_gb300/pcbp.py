@@ -21,6 +21,7 @@ PC_NMAX = 2048
 PC_MAX_EVENTS = 32
 
 EXPORTED = ("pc_construct", "pc_encode", "bp_decode_workspace_size", "bp_decode", "bp_decode_host", "bp_decode_trace",
+            "bp_decode_posterior", "pc_f_eval",
             "bp_decode_noalloc", "pc_partition_selfcheck", "pc_build_info", "bp_kernel_threads", "bp_slot_limit",
             "bp_mixed_table_size", "bp_mixed_prepare", "bp_mixed_workspace_size", "bp_decode_mixed",
             "wbp_weights_count", "wbp_ckpt_count", "wbp_workspace_size", "wbp_forward", "wbp_backward",
@@ -68,6 +69,9 @@ _lib.bp_decode_host.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_
                                 _vp, _vp]
 _lib.bp_decode_trace.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64,
                                  C.POINTER(PcEvent), C.c_int32, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.bp_decode_posterior.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
+                                     _vp, _vp, _vp, _vp]
+_lib.pc_f_eval.argtypes = [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_float, _vp]
 _lib.bp_decode_noalloc.argtypes = [C.POINTER(PcCode), _vp, C.POINTER(PcSched), C.c_int32, C.c_int64, _vp, _vp,
                                    _vp, _vp]
 _lib.pc_partition_selfcheck.argtypes = [_vp, _vp]
@@ -248,6 +252,33 @@ def bp_decode_trace(code: PcCode, llr, sch: PcSched, max_iters: int, events, dum
     _check("bp_decode_trace", _lib.bp_decode_trace(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B, evp, nev,
                                                    _ptr(dump), _ptr(bits), _ptr(iters), _ptr(crc_ok),
                                                    _ptr(workspace), _stream(stream)))
+
+
+def bp_decode_posterior(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, post, workspace,
+                        stream=None):
+    """bp_decode that also writes post [B, 2, N] float32: L at node level n+1 and R at node level 1
+    after each frame's last iteration (N >= 128, no G-matrix stop)."""
+    import torch
+
+    B = llr.shape[0]
+    _require("bp_decode_posterior", *_decode_checks(code, llr, bits, iters, crc_ok, "cuda"),
+             (post, torch.float32, (B, 2, code.N), "cuda"))
+    _require_workspace("bp_decode_posterior", workspace, bp_decode_workspace_size(code, B))
+    _require_stream("bp_decode_posterior", stream)
+    _check("bp_decode_posterior", _lib.bp_decode_posterior(C.byref(code), _ptr(llr), C.byref(sch), max_iters, B,
+                                                           _ptr(bits), _ptr(iters), _ptr(crc_ok), _ptr(post),
+                                                           _ptr(workspace), _stream(stream)))
+
+
+def pc_f_eval(a, b, out, fkind: int, alpha: float = 1.0, stream=None):
+    """out = f(a, b) elementwise as the decoder kernels evaluate it (float32 CUDA tensors of one shape)."""
+    import torch
+
+    shape = tuple(a.shape)
+    _require("pc_f_eval", (a, torch.float32, shape, "cuda"), (b, torch.float32, shape, "cuda"),
+             (out, torch.float32, shape, "cuda"))
+    _require_stream("pc_f_eval", stream)
+    _check("pc_f_eval", _lib.pc_f_eval(_ptr(a), _ptr(b), _ptr(out), a.numel(), fkind, alpha, _stream(stream)))
 
 
 def bp_decode_noalloc(code: PcCode, llr, sch: PcSched, max_iters: int, bits, iters, crc_ok, stream=None):

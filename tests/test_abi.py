@@ -397,3 +397,30 @@ def test_binding_rejects_tensors_of_another_device(pcbp, monkeypatch):
         with pytest.raises(pcbp.PcError) as e:
             call()
         assert e.value.status == pcbp.PC_EINVAL
+
+
+@no_gpu_only
+def test_posterior_and_f_eval_validate_before_touching_the_device(pcbp):
+    """bp_decode_posterior refuses lengths that run another kernel, the G-matrix stop and a missing
+    output; pc_f_eval refuses an unknown f and a negative count; all on the host."""
+    p = C.c_void_p
+    s = pcbp.sched(mode=1, P_range=3, P_level=5, N_min=5, T0=5)
+    code = pcbp.pc_construct(256, 128, 8, 0x9B)
+    small = pcbp.pc_construct(64, 32, 8, 0x9B)
+    post = pcbp._lib.bp_decode_posterior
+
+    def call(c, sch, out=p(65536), B=4):
+        return post(C.byref(c), p(4096), C.byref(sch), 10, B, p(8192), p(12288), p(16384), out, p(32768), None)
+
+    assert call(small, s) == pcbp.PC_EUNSUPPORTED                  # N < 128: another kernel
+    assert call(code, pcbp.sched(stop_kind=3)) == pcbp.PC_EUNSUPPORTED
+    assert call(code, s, out=None) == pcbp.PC_EINVAL
+    assert call(code, s, out=p(65536 + 2)) == pcbp.PC_EINVAL        # misaligned
+    assert call(code, pcbp.sched(mode=3)) == pcbp.PC_EINVAL
+    assert call(code, s, B=0) == pcbp.PC_OK
+    f = pcbp._lib.pc_f_eval
+    assert f(p(4096), p(8192), p(12288), 10, 2, 1.0, None) == pcbp.PC_EINVAL
+    assert f(p(4096), p(8192), p(12288), -1, 0, 1.0, None) == pcbp.PC_EINVAL
+    assert f(None, p(8192), p(12288), 10, 0, 1.0, None) == pcbp.PC_EINVAL
+    assert f(p(4098), p(8192), p(12288), 10, 0, 1.0, None) == pcbp.PC_EINVAL
+    assert f(None, None, None, 0, 1, 1.0, None) == pcbp.PC_OK
