@@ -395,7 +395,38 @@ def run_variants(pcbp, inputs, dev, warmup):
         out[name] = {"gbit_s": B * (K - R_CRC) / (ms / 1e3) / 1e9, "ms": ms, "max_iters": max_iters,
                      "fer": errors / B, "fer_ci95": wilson(errors, B),
                      "mean_iters": float(dec.iters.double().mean().item())}
+        if name == "ppbp_boxplus":
+            # the first frames, for the FP64 oracle of the CPU-baseline leg
+            out["_boxplus_sample"] = {"llr": llr[:BOXPLUS_ORACLE_FRAMES].cpu().numpy(),
+                                      "pay": pay[:BOXPLUS_ORACLE_FRAMES].cpu().numpy(),
+                                      "bits": got[:BOXPLUS_ORACLE_FRAMES].cpu().numpy(),
+                                      "iters": dec.iters[:BOXPLUS_ORACLE_FRAMES].cpu().numpy(), "kw": kw}
     return out
+
+
+BOXPLUS_ORACLE_FRAMES = 16384
+
+
+def boxplus_oracle_check(sample, gpu_row):
+    """FP64 oracle (exact box-plus) on the first frames of the box-plus variant: its FER and
+    Wilson interval beside the GPU's, and the share of frames decided identically."""
+    import numpy as np
+
+    import oracle as O
+
+    _, fr = O.construct(N, K)
+    B = len(sample["llr"])
+    t0 = time.perf_counter()
+    u, it, _ = O.decode_batch(fr, R_CRC, POLY, sample["llr"].astype(np.float64), O.Sched(**sample["kw"]), MAX_ITERS,
+                              dtype=np.float64)
+    secs = time.perf_counter() - t0
+    got = O.info_bits(u, fr)[:, : K - R_CRC]
+    errs = int((got != sample["pay"]).any(axis=1).sum())
+    ci = wilson(errs, B)
+    return {"frames": B, "fer": errs / B, "fer_ci95": ci, "seconds": secs, "cores": O.max_threads(),
+            "gpu_fer_inside": bool(ci[0] <= gpu_row["fer"] <= ci[1]),
+            "identical_decisions": float(np.mean(np.all(got == sample["bits"], axis=1))),
+            "identical_iterations": float(np.mean(it == sample["iters"])), "dtype": "f64"}
 
 
 SWEEP_EBN0 = tuple(1.5 + 0.25 * i for i in range(11))
@@ -754,8 +785,10 @@ def run_ours(args):
     if rank == 0 and not args.no_wbp:
         line["wbp"] = run_wbp(pcbp, inputs, dev, args.steps, args.warmup)
 
+    boxplus_sample = None
     if rank == 0 and not args.no_variants:
         line["variants"] = run_variants(pcbp, inputs, dev, args.warmup)
+        boxplus_sample = line["variants"].pop("_boxplus_sample", None)
 
     if rank == 0 and not args.no_mixed:
         del dec
@@ -772,6 +805,9 @@ def run_ours(args):
                                 "mean_iters": cb["mean_iters"],
                                 "value_1core": cb1["gbps"],
                                 "sample_1core": f"{cb1['frames']} frames, {cb1['seconds']:.1f} s on 1 core"}
+        if boxplus_sample is not None:
+            line["variants"]["ppbp_boxplus"]["oracle"] = boxplus_oracle_check(boxplus_sample,
+                                                                             line["variants"]["ppbp_boxplus"])
         lo, hi_ = line["cpu_baseline"]["fer_ci95"]
         line["fer_matched"] = bool(lo <= line["fer"] <= hi_ or line["fer_ci95"][0] <= cb["fer"] <= line["fer_ci95"][1])
     if rank == 0:
