@@ -61,8 +61,7 @@ int occupancy(const LaunchGeom& g)
 void PCBP_CAT(bp3_shape_, PCBP_LOGN)(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out)
 {
     *threads_per_slot_out = Geo::T;
-    *slot_bytes_out = align16(sizeof(Ctl3<PCBP_LOGN, KB>)) + align16(2 * Geo::NW * 4) +
-                      size_t(2 * Geo::NPL) * Geo::N * 4;
+    *slot_bytes_out = tmem_slot_bytes<PCBP_LOGN, KB>();
     int slots = tmem_max_threads<PCBP_LOGN, KB>() / Geo::T;
     const int by_tmem = Geo::MAX_WARPS_TMEM / (Geo::T / 32);
     slots = slots < by_tmem ? slots : by_tmem;

@@ -112,11 +112,15 @@ __host__ __device__ constexpr int reverse_bits(int e)
     return r;
 }
 
-// TMEM columns of one group's interior messages (E per level): group 0 skips
-// L level 1 (registers), the last group keeps its L in registers.
+// TMEM columns of one group's interior messages (E per level): L at levels
+// s0+2 .. s0+gl and R at levels s0+2 .. s0+gl.  L at level s0+1 (the group's
+// input) stays in its shared-memory boundary plane, where the R sweep reads it
+// again (group 0: the channel LLRs, in registers); the last group keeps its L
+// in registers.
 __host__ __device__ constexpr int group_cols(int s0, int gl, bool single, bool last, int E)
 {
-    return single ? 0 : (last ? (gl - 1) * E : (s0 == 0 ? (2 * gl - 2) * E : (2 * gl - 1) * E));
+    (void)s0;
+    return single ? 0 : (last ? (gl - 1) * E : 2 * (gl - 1) * E);
 }
 
 // Interior columns (cols) and register groups (groups) of the partition
@@ -190,10 +194,20 @@ struct G3 {
     static constexpr PartitionSize MAXP = max_partition(LOGN, KB);
     static constexpr int COLS = MAXP.cols;                       // interior messages
     static constexpr int ACOL = COLS;                            // E shared-memory offsets per register group
-    static constexpr int PCOL = ACOL + MAXP.groups * E;          // the last group's priors
-    static constexpr int CCOL = PCOL + E;                        // the last group's CRC contributions
-    static constexpr int TCOLS = CCOL + E;                       // TMEM columns per thread
+    static constexpr int TCOLS = ACOL + MAXP.groups * E;         // TMEM columns per thread
     static constexpr int MAX_WARPS_TMEM = 4 * (512 / TCOLS);
+    // Shared-memory planes of a frame slot, N floats each, in the swizzled
+    // position order: plane p < n holds R at node level p+2 (p < n-1) and, while
+    // level p+2 is interior to the group that starts at stage p, L at node level
+    // p+1, the input boundary of that group (its canonical R copy is dead while
+    // the partition stands: the group keeps those R messages in TMEM; plane n-1,
+    // level n+1, holds only L); plane n holds L at level 2 between two single
+    // stages; planes n+1 and n+2 hold the priors R(n+1) and the CRC
+    // contributions c_j of the positions.
+    static constexpr int NPLANES = LOGN + 3;
+    static constexpr int SPARE = LOGN;
+    static constexpr int PRIOR = LOGN + 1;
+    static constexpr int CJ = LOGN + 2;
     static_assert(T >= 32, "every lane of a warp owns positions");
 };
 
@@ -233,12 +247,13 @@ __device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned 
 // 8.00 against 9.51 ms, N = 2048 16.9 against 20.4 ms).
 __host__ __device__ constexpr int tmem_default_kb(int logn) { return logn <= 9 ? 2 : 3; }
 
-// Largest CTA of the TMEM kernel for a length: 512 threads, or fewer when
-// shared memory or TMEM holds fewer slots (N = 1024: 3 slots of 128 threads).
+// Largest CTA of the TMEM kernel for a length: as many frame slots as shared
+// memory and TMEM hold (N = 1024: 4 slots of 128 threads; N = 2048: one slot
+// of 256), at most 768 threads.
 template <int LOGN, int KB>
 __host__ __device__ constexpr int tmem_max_threads()
 {
-    return KB == 3 ? (LOGN == 10 ? 384 : (LOGN >= 11 ? 256 : 512)) : (LOGN >= 11 ? 512 : 768);
+    return KB == 3 ? (LOGN == 10 ? 512 : (LOGN >= 11 ? 256 : 512)) : (LOGN >= 11 ? 512 : 768);
 }
 
 // Per-slot control block: the stage partition plus a packed copy that the
@@ -248,8 +263,8 @@ struct Ctl3 {
     GroupCtl<LOGN, KB> g;
     // rec[gi] = {s0 | gl << 8 | single << 16 | local << 24 | (boundary gi|gi+1 warp-local) << 25
     //              | (boundary gi-1|gi warp-local) << 26,
-    //            TMEM column of L level s0+1 (virtual for group 0 and the last group;
-    //            R level s0+2 is at this + gl E),
+    //            TMEM column of L level s0+2 (virtual for the last group;
+    //            R level s0+2 is at this + (gl - 1) E),
     //            contig(class 0) & 0xff | (contig(class 1) & 0xff) << 8,
     //            TMEM column of the group's cached shared-memory offsets}
     int4 rec[LOGN];
@@ -258,6 +273,14 @@ struct Ctl3 {
     unsigned crc_part[3];    // CRC residue of iteration it, accumulated in crc_part[it % 3]
     unsigned pad_;
 };
+
+// Bytes of one frame slot: control block, decision words, NPLANES planes.
+template <int LOGN, int KB>
+__host__ __device__ constexpr size_t tmem_slot_bytes()
+{
+    return align16(sizeof(Ctl3<LOGN, KB>)) + align16(size_t(2 * G3<LOGN, KB>::NW * 4)) +
+           size_t(G3<LOGN, KB>::NPLANES) * (size_t(1) << LOGN) * 4;
+}
 
 // ---------------------------------------------------------------------------
 // tcgen05 data movement between registers and this thread's TMEM lane.
@@ -360,8 +383,8 @@ __device__ __noinline__ void pack_groups(Ctl3<LOGN, KB>* c)
     for (int gi = 0; gi < ng; ++gi) {
         const int s0 = c->g.s0[gi], gl = c->g.g[gi], single = c->g.single_[gi];
         const bool last = gi == ng - 1;
-        // L level s0+1+i at colL + i E, R level s0+2+i at colL + (gl + i) E
-        const int colL = last ? col - gl * E : (s0 == 0 ? col - E : col);
+        // L level s0+2+i at colL + i E, R level s0+2+i at colL + (gl - 1 + i) E
+        const int colL = last ? col - (gl - 1) * E : col;
         const bool wl_after = gi + 1 < ng && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi + 1);
         const bool wl_before = gi > 0 && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi - 1);
         c->rec[gi] = make_int4(s0 | (gl << 8) | (single << 16) | (int(c->g.local[gi]) << 24) | (int(wl_after) << 25) |
@@ -498,7 +521,7 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
             }
             last_s0 = st; last_gl = gl; last_kind = kind;
             if (kind != 2) {
-                col += (st == 0 ? 2 * gl - 2 : 2 * gl - 1) * E;   // the last group is corrected below
+                col += 2 * (gl - 1) * E;   // the last group's columns are counted from its R levels below
                 acol += E;
             }
             ++ng;
@@ -559,8 +582,8 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
     if (mine && cls == 0) {
         const bool wl_after = !last && wb != ~0u && wb == wb_next;
         const bool wl_before = gi > 0 && wb != ~0u && wb == wb_prev;
-        // columns of L level s0+1 (virtual for group 0 and the last group), as pack_groups
-        const int colL = last ? my_col - my_gl * E : (my_s0 == 0 ? my_col - E : my_col);
+        // column of L level s0+2 (virtual for the last group), as pack_groups
+        const int colL = last ? my_col - (my_gl - 1) * E : my_col;
         c->rec[gi] = make_int4(my_s0 | (my_gl << 8) | (int(single) << 16) | (int(my_kind != 0) << 24) |
                                    (int(wl_after) << 25) | (int(wl_before) << 26),
                                colL, (contig & 0xff) | ((contig1 & 0xff) << 8), single ? 0 : my_acol);
@@ -640,12 +663,14 @@ __device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S,
 
 // One permuted stage s narrower than a register group (m < KB events), with
 // per-PE addressing: the L sweep (r_sweep false) or the R sweep of stage s.
-// The R sweep of stage 0 sets the hard-decision bits of L + R at node level 1
-// in xh, or, when post1 is given, writes R at node level 1 there instead.
-// E/2 PEs per thread; out of line (rare).
+// L at node level s+1 comes from Lin (the channel LLRs for s = 0), L at level
+// s+2 goes to Lout, R at level l is plane l-2 of Rp.  The R sweep of stage 0
+// sets the hard-decision bits of L + R at node level 1 in xh, or, when post1
+// is given, writes R at node level 1 there instead.  E/2 PEs per thread; out
+// of line (rare).
 template <int LOGN, int E, int T, int FK>
 __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowmask, int beta, int lo, int m1, int pbit,
-                                          const float* llr_f, float* Lp, float* Rp, uint32_t* xh,
+                                          const float* llr_f, const float* Lin, float* Lout, float* Rp, uint32_t* xh,
                                           const unsigned char* s_swz, float alpha, unsigned* check,
                                           float* post1 = nullptr)
 {
@@ -667,13 +692,13 @@ __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowm
 #else
         (void)check;
 #endif
-        const float lt = s == 0 ? llr_f[t] : Lp[(s - 1) * N + sw(t)];
-        const float lb = s == 0 ? llr_f[b] : Lp[(s - 1) * N + sw(b)];
+        const float lt = s == 0 ? llr_f[t] : Lin[sw(t)];
+        const float lb = s == 0 ? llr_f[b] : Lin[sw(b)];
         const float rt = Rp[s * N + sw(t)];
         const float rb = Rp[s * N + sw(b)];
         if (!r_sweep) {
-            Lp[s * N + sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
-            Lp[s * N + sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
+            Lout[sw(t)] = fnode<FK>(lt, __fadd_rn(lb, rb), alpha);
+            Lout[sw(b)] = __fadd_rn(fnode<FK>(rt, lt, alpha), lb);
         } else {
             const float o1 = fnode<FK>(rt, __fadd_rn(lb, rb), alpha);
             const float o2 = __fadd_rn(fnode<FK>(rt, lt, alpha), rb);
@@ -755,15 +780,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const int lane = tid & 31;
     const int warp = tid >> 5;
     constexpr size_t ctl_bytes = align16(sizeof(Ctl));
-    constexpr size_t slot_sz = ctl_bytes + align16(size_t(2 * NW * 4)) + size_t(2 * NPL) * N * 4;
+    constexpr size_t slot_sz = tmem_slot_bytes<LOGN, KB>();
     const Ctl* tmpl = reinterpret_cast<const Ctl*>(smem + tmem_table_bytes(N, K));
     unsigned char* sbase = smem + tmem_cta_bytes<LOGN, KB>(N, K) + size_t(slot) * slot_sz;
     Ctl* ctl = reinterpret_cast<Ctl*>(sbase);
     uint32_t* dec = reinterpret_cast<uint32_t*>(sbase + ctl_bytes);
     uint32_t* xh = dec + NW;
-    float* Lp = reinterpret_cast<float*>(sbase + ctl_bytes + align16(2 * NW * 4));   // level l at (l-2)*N
-    float* Rp = Lp + NPL * N;                                                          // level l at (l-2)*N
-    const int lp_off = int(reinterpret_cast<unsigned char*>(Lp) - smem);
+    // the slot's planes (G3::NPLANES): R at node level l in plane l-2
+    float* Rp = reinterpret_cast<float*>(sbase + ctl_bytes + align16(2 * NW * 4));
+    float* Lspare = Rp + Geo::SPARE * N;
+    const int lp_off = int(reinterpret_cast<unsigned char*>(Rp) - smem);
     const unsigned bar_id = 1u + unsigned(slot);
     auto sync = [&]() {
         if (T == 32) __syncwarp();
@@ -774,13 +800,18 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const uint32_t tm = tm_base + (uint32_t(32 * (gwarp & 3)) << 16) + uint32_t((gwarp >> 2) * Geo::TCOLS);
 
     // The cached offset A of a position in a group with first stage s0 is the
-    // byte offset (from smem) of the position in L plane s0-1 (node level
-    // s0+1); the group's other planes are at fixed distances:
-    //   Lp plane s0-1+d at A + 4 d N,   Rp plane s0-1+d at A + 4 (NPL + d) N.
+    // byte offset (from smem) of the position in plane s0, which holds the
+    // group's input, L at node level s0+1; the other planes it touches are at
+    // fixed distances, plane s0+d at A + 4 d N:
+    //   R at level s0+1 (the R sweep's output)        d = -1
+    //   R at level s0+2+i (interior, copied at switches) d = i
+    //   R at level s0+gl+1 (the next group's output)  d = gl - 1
+    //   L at level s0+gl+1 (the next group's input)   d = gl
+    //   priors, CRC contributions (last group, s0 = n - gl)  d = gl + 1, gl + 2
     auto at = [&](int a, int floats) -> float& {
         int off = a + 4 * floats;
 #ifdef PCBP_CHECKED
-        if (off < lp_off || off > lp_off + 4 * (2 * NPL * N - 1) || (off & 3)) {
+        if (off < lp_off || off > lp_off + 4 * (Geo::NPLANES * N - 1) || (off & 3)) {
             chk_fail(J.check, 0);
             off = lp_off;
         }
@@ -799,7 +830,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     };
     // logical position of cached offset a in a group with first stage s0
     auto pos_of = [&](int a, int s0) {
-        int x = ((a - lp_off) >> 2) - (s0 - 1) * N;
+        int x = ((a - lp_off) >> 2) - s0 * N;
 #ifdef PCBP_CHECKED
         if (x < 0 || x >= N) {
             chk_fail(J.check, 2);
@@ -825,6 +856,18 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         return (local && ((tid & lowmask) == ctl->g.beta)) ? 1 : 0;
     };
 
+    // Planes of a single stage's L input (level s0+1) and output (level s0+2):
+    // the boundary plane of its level, or the spare plane where the
+    // neighbouring stage is a single stage too (its boundary plane then holds
+    // a boundary R message).  Partitions have at most KB - 1 <= 2 single stages.
+    auto single_in = [&](int gi, int s0) -> const float* {
+        if (s0 == 0) return nullptr;
+        return ((ctl->rec[gi - 1].x >> 16) & 1) ? Lspare : Rp + s0 * N;
+    };
+    auto single_out = [&](int gi, int s0) -> float* {
+        return ((ctl->rec[gi + 1].x >> 16) & 1) ? Lspare : Rp + (s0 + 1) * N;
+    };
+
     // A new frame on the partition the TMEM caches already describe: zero
     // interior R messages, channel LLRs of group 0's positions.
     auto restart_partition = [&](const float* llr_f) {
@@ -837,7 +880,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             const int4 rc = ctl->rec[gi];
             const int gl = (rc.x >> 8) & 0xff;
             if ((rc.x >> 16) & 1) continue;
-            const uint32_t colR = uint32_t(rc.y + gl * E);
+            const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) tm_st<E>(tc(colR + uint32_t(i * E)), z);
             if (gi == 0) {
@@ -852,10 +895,9 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         tm_wait_st();
     };
 
-    // After a new partition: cache the register groups' offsets and the last
-    // group's priors and CRC contributions in TMEM, move the interior R
-    // messages from the canonical planes to TMEM, load the channel LLRs of the
-    // first group.
+    // After a new partition: cache the register groups' offsets in TMEM, move
+    // the interior R messages from the canonical planes to TMEM, load the
+    // channel LLRs of the first group.
     auto enter_partition = [&](const float* llr_f) {
         const int ng = ctl->g.ng;
         #pragma unroll 1
@@ -874,27 +916,15 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
 #endif
 #pragma unroll
-            for (int e = 0; e < E; ++e) A[e] = lp_off + 4 * ((s0 - 1) * N + ph[e]);
+            for (int e = 0; e < E; ++e) A[e] = lp_off + 4 * (s0 * N + ph[e]);
             tm_st_i<E>(tc(uint32_t(rc.w)), A);
-            const uint32_t colR = uint32_t(rc.y + gl * E);
+            const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
             #pragma unroll 1
-            for (int i = 0; i < gl - 1; ++i) {     // R level s0+2+i: Rp plane s0+i
+            for (int i = 0; i < gl - 1; ++i) {     // R level s0+2+i: plane s0+i
                 float v[E];
 #pragma unroll
-                for (int e = 0; e < E; ++e) v[e] = at(A[e], (NPL + i + 1) * N);
+                for (int e = 0; e < E; ++e) v[e] = at(A[e], i * N);
                 tm_st<E>(tc(colR + uint32_t(i * E)), v);
-            }
-            if (gi == ng - 1) {
-                float pr[E];
-                int cj[E];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const int j = sw(ph[e]);
-                    pr[e] = prior_of(s_frozen, j);
-                    cj[e] = int(s_cj[j]);
-                }
-                tm_st<E>(tc(uint32_t(Geo::PCOL)), pr);
-                tm_st_i<E>(tc(uint32_t(Geo::CCOL)), cj);
             }
             if (gi == 0) {
 #pragma unroll
@@ -917,7 +947,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             tm_ld_i<E>(tc(uint32_t(rc.w)), A);
             tm_wait_ld();
             tm_fence<E>(A);
-            const uint32_t colR = uint32_t(rc.y + gl * E);
+            const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {
                 float v[E];
@@ -925,7 +955,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 tm_wait_ld();
                 tm_fence<E>(v);
 #pragma unroll
-                for (int e = 0; e < E; ++e) at(A[e], (NPL + i + 1) * N) = v[e];
+                for (int e = 0; e < E; ++e) at(A[e], i * N) = v[e];
             }
         }
     };
@@ -942,6 +972,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         }
     };
     bool fresh = false;     // the control block holds the no-event partition and the TMEM caches match it
+    // the prior R(n+1) and the CRC contribution of every position, in this slot's planes (read
+    // by the last group at fixed distances from its cached offsets)
+    for (int j = tid; j < N; j += T) {
+        Rp[Geo::PRIOR * N + sw(j)] = prior_of(s_frozen, j);
+        Rp[Geo::CJ * N + sw(j)] = __int_as_float(int(s_cj[j]));
+    }
     while (true) {
         fetch_next();
         if (tid == 0) {
@@ -971,8 +1007,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 reinterpret_cast<int4*>(ctl)[i] = reinterpret_cast<const int4*>(tmpl)[i];
         }
         sync();
-        if (fresh) restart_partition(llr_f);
-        else enter_partition(llr_f);
+        if (fresh) {
+            restart_partition(llr_f);
+        } else {
+            // enter_partition reads the interior R planes, which the first L sweep overwrites
+            // with boundary L messages: every thread's reads come first
+            enter_partition(llr_f);
+            sync();
+        }
         fresh = true;
 
         int next_reset = S.mode == 1 ? S.T0 : (S.mode == 2 ? S.it_reset_full : 0);
@@ -998,8 +1040,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 if (SINGLES && ((rc.x >> 16) & 1)) {
                     // one permuted stage with per-PE addressing (m < KB events)
                     single_stage<LOGN, E, T, FK>(false, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
-                                                 ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp, Rp,
-                                                 xh, s_swz, alpha, J.check);
+                                                 ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f,
+                                                 single_in(gi, s0), single_out(gi, s0), Rp, xh, s_swz, alpha, J.check);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
@@ -1009,25 +1051,24 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         tm_ld_i<E>(tc(uint32_t(rc.w)), A);
                         if constexpr (GL > 1) {
 #pragma unroll
-                            for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tc(colL + uint32_t((GL + i) * E)), rp[i]);
+                            for (int i = 0; i < GL - 1; ++i) tm_ld<E>(tc(colL + uint32_t((GL - 1 + i) * E)), rp[i]);
                         }
                         tm_wait_ld();
                         tm_fence<E>(A);
                         float x[E], rb[E];
 #pragma unroll
                         for (int e = 0; e < E; ++e) {
-                            x[e] = FIRST ? L1[e] : at(A[e], 0);
-                            rb[e] = at(A[e], (NPL + GL) * N);                 // R level s0+GL+1 (boundary)
+                            x[e] = FIRST ? L1[e] : at(A[e], 0);                  // L level s0+1 (boundary)
+                            rb[e] = at(A[e], (GL - 1) * N);                      // R level s0+GL+1 (boundary)
                         }
                         if constexpr (GL > 1) {
 #pragma unroll
                             for (int i = 0; i < GL - 1; ++i) tm_fence<E>(rp[i]);
                         }
-                        if constexpr (!FIRST) tm_st<E>(tc(colL), x);       // L level s0+1
 #pragma unroll
                         for (int i = 0; i < GL; ++i) {
                             l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
-                            if (i < GL - 1) tm_st<E>(tc(colL + uint32_t((i + 1) * E)), x);   // L level s0+2+i
+                            if (i < GL - 1) tm_st<E>(tc(colL + uint32_t(i * E)), x);   // L level s0+2+i
                         }
 #pragma unroll
                         for (int e = 0; e < E; ++e) at(A[e], GL * N) = x[e];          // L level s0+GL+1
@@ -1075,18 +1116,20 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 float x[E];
                 int cj[E];
                 tm_ld_i<E>(tc(uint32_t(rcL.w)), AL);
-                tm_ld<E>(tc(uint32_t(Geo::PCOL)), pr);
-                tm_ld_i<E>(tc(uint32_t(Geo::CCOL)), cj);
 #pragma unroll
-                for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tc(colLL + uint32_t((GLL + i) * E)), rp[i]);
+                for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tc(colLL + uint32_t((GLL - 1 + i) * E)), rp[i]);
                 tm_wait_ld();
                 tm_fence<E>(AL);
-                tm_fence<E>(pr);
-                tm_fence<E>(cj);
 #pragma unroll
                 for (int i = 0; i < GLL - 1; ++i) tm_fence<E>(rp[i]);
+                // the last group ends at stage n-1, so it starts at s0 = n - GLL (never 0): its
+                // input, priors and CRC contributions are planes n-GLL, n+1 and n+2
 #pragma unroll
-                for (int e = 0; e < E; ++e) x[e] = at(AL[e], 0);   // the last group never starts at stage 0
+                for (int e = 0; e < E; ++e) {
+                    x[e] = at(AL[e], 0);
+                    pr[e] = at(AL[e], (GLL + 1) * N);
+                    cj[e] = __float_as_int(at(AL[e], (GLL + 2) * N));
+                }
 #pragma unroll
                 for (int i = 0; i < GLL; ++i) {
 #pragma unroll
@@ -1144,10 +1187,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 for (int i = GLL - 1; i >= 0; --i) {
                     r_layer<E, FK>(y, xL[i], i, alpha);
                     if (i > 0) {
-                        tm_st<E>(tc(colLL + uint32_t((GLL + i - 1) * E)), y);   // R level s0L+1+i
+                        tm_st<E>(tc(colLL + uint32_t((GLL + i - 2) * E)), y);   // R level s0L+1+i
                     } else {
 #pragma unroll
-                        for (int e = 0; e < E; ++e) at(AL[e], NPL * N) = y[e];   // R level s0L+1
+                        for (int e = 0; e < E; ++e) at(AL[e], -N) = y[e];       // R level s0L+1
                     }
                 }
             };
@@ -1204,9 +1247,9 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 if (SINGLES && ((rc.x >> 16) & 1)) {
                     if (!FIRST || want_g || PO)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
-                                                     ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f, Lp,
-                                                     Rp, xh, s_swz, alpha, J.check,
-                                                     (PO && FIRST) ? J.post + size_t(f) * 2 * N + N : nullptr);
+                                                     ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f,
+                                                     single_in(gi, s0), single_out(gi, s0), Rp, xh, s_swz, alpha,
+                                                     J.check, (PO && FIRST) ? J.post + size_t(f) * 2 * N + N : nullptr);
                 } else {
                     const uint32_t colL = uint32_t(rc.y);
                     auto body = [&](auto glc) {
@@ -1215,28 +1258,26 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         float lv[GL][E];
                         tm_ld_i<E>(tc(uint32_t(rc.w)), A);
 #pragma unroll
-                        for (int i = 0; i < GL; ++i)
-                            if (i > 0 || !FIRST) tm_ld<E>(tc(colL + uint32_t(i * E)), lv[i]);   // L level s0+1+i
+                        for (int i = 1; i < GL; ++i) tm_ld<E>(tc(colL + uint32_t((i - 1) * E)), lv[i]);   // L level s0+1+i
                         tm_wait_ld();
                         tm_fence<E>(A);
                         float y[E];
 #pragma unroll
-                        for (int e = 0; e < E; ++e) y[e] = at(A[e], (NPL + GL) * N);           // R level s0+GL+1
-#pragma unroll
-                        for (int i = 0; i < GL; ++i) tm_fence<E>(lv[i]);
-                        if constexpr (FIRST) {
-#pragma unroll
-                            for (int e = 0; e < E; ++e) lv[0][e] = L1[e];
+                        for (int e = 0; e < E; ++e) {
+                            y[e] = at(A[e], (GL - 1) * N);                                // R level s0+GL+1
+                            lv[0][e] = FIRST ? L1[e] : at(A[e], 0);                       // L level s0+1 (boundary)
                         }
+#pragma unroll
+                        for (int i = 1; i < GL; ++i) tm_fence<E>(lv[i]);
 #pragma unroll
                         for (int i = GL - 1; i >= 0; --i) {
                             if (FIRST && i == 0 && !want_g && !PO) continue;      // stage 0 writes only the G-matrix bits
                             r_layer<E, FK>(y, lv[i], i, alpha);
                             if (i > 0) {
-                                tm_st<E>(tc(colL + uint32_t((GL + i - 1) * E)), y);            // R level s0+1+i
+                                tm_st<E>(tc(colL + uint32_t((GL + i - 2) * E)), y);            // R level s0+1+i
                             } else if (!FIRST) {
 #pragma unroll
-                                for (int e = 0; e < E; ++e) at(A[e], NPL * N) = y[e];           // R level s0+1
+                                for (int e = 0; e < E; ++e) at(A[e], -N) = y[e];                // R level s0+1
                             } else if (PO) {
                                 float* po = J.post + size_t(f) * 2 * N + N;      // R at node level 1
 #pragma unroll
