@@ -1107,6 +1107,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             int AL[E];
             float pr[E];     // R(n+1): the prior of the last group's positions
             unsigned umask = 0;
+            unsigned pmask = 0;     // G-matrix test: the decisions at their position bits within the block
             const bool check = S.stop_kind != 0 && it >= S.stop_from;
             // the group's stage count as a compile-time constant
             auto last_body = [&](auto glc) {
@@ -1146,7 +1147,6 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 // a5: decisions u_j = [L(n+1) + R(n+1) < 0], taken as L(n+1) < -R(n+1) (a
                 // rounded sum has the sign of the exact one), and their CRC residue
                 unsigned part = 0;
-                unsigned pmask = 0;     // G-matrix test: the decisions at their position bits within the block
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const bool u = x[e] < -pr[e];
@@ -1157,26 +1157,6 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 if (check && want_crc) {
                     part = __reduce_xor_sync(0xffffffffu, part);
                     if (lane == 0 && part) atomicXor(&ctl->crc_part[pb], part);
-                }
-                if (want_g) {
-                    if (!((rcL.x >> 24) & 1) && int((signed char)(rcL.z & 0xff)) == 0) {
-                        // the register bits are position bits 0..KB-1 (every thread in class 0,
-                        // in stage order): a thread's decisions lie in one E-bit field of the word
-                        // it shares with 32/E neighbouring lanes, combined by shuffles and stored once
-                        // (register e at position base + last_group_offset(e), base E-aligned)
-                        const int base = pos_of(AL[0], s0L);
-                        unsigned v = pmask << (base & 31);
-#pragma unroll
-                        for (int o = 1; o < 32 / E; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
-                        if ((lane & (32 / E - 1)) == 0) dec[base >> 5] = v;
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < E; ++e)
-                            if ((umask >> e) & 1u) {
-                                const int j = pos_of(AL[e], s0L);
-                                atomicOr(&dec[j >> 5], 1u << (j & 31));
-                            }
-                    }
                 }
                 // R sweep of the last group (ahead of the stop test)
                 tm_wait_st();
@@ -1204,6 +1184,37 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if (tid == 0) ctl->crc_part[pb == 0 ? 2 : pb - 1] = 0u;
 
             bool po_end = false;     // PO: the frame's last iteration, finished after its R sweep
+            // the G-matrix test runs where it can decide: from stop_from on, and with the combined
+            // stop only where the CRC residue is zero (otherwise the frame goes on either way)
+            const bool gtest = want_g && check && (!want_crc || res == 0u);
+            if (want_g && (gtest || it == max_iters)) {
+                // the decision words of this iteration, into cleared words (every word is clear
+                // except after a G-matrix test, which clears them again)
+                if (!((rcL.x >> 24) & 1) && int((signed char)(rcL.z & 0xff)) == 0) {
+                    // the register bits are position bits 0..KB-1 (every thread in class 0, in
+                    // stage order): a thread's decisions lie in one E-bit field of the word it
+                    // shares with 32/E neighbouring lanes, combined by shuffles and stored once
+                    // (register e at position base + last_group_offset(e), base E-aligned)
+                    const int base = pos_of(AL[0], s0L);
+                    unsigned v = pmask << (base & 31);
+#pragma unroll
+                    for (int o = 1; o < 32 / E; o <<= 1) v |= __shfl_xor_sync(0xffffffffu, v, o);
+                    if ((lane & (32 / E - 1)) == 0) dec[base >> 5] = v;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < E; ++e)
+                        if ((umask >> e) & 1u) {
+                            const int j = pos_of(AL[e], s0L);
+                            atomicOr(&dec[j >> 5], 1u << (j & 31));
+                        }
+                }
+                if (!gtest) {
+                    // the last iteration without a test: the frame ends here, without its R sweep
+                    fetch_next();
+                    sync();
+                    break;
+                }
+            }
             if (!want_g) {
                 const bool stop = check && res == 0u;
                 if (stop || it == max_iters) {
@@ -1245,7 +1256,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 const int4 rc = ctl->rec[gi];
                 const int s0 = FIRST ? 0 : (rc.x & 0xff), gl = (rc.x >> 8) & 0xff;
                 if (SINGLES && ((rc.x >> 16) & 1)) {
-                    if (!FIRST || want_g || PO)
+                    if (!FIRST || gtest || PO)
                         single_stage<LOGN, E, T, FK>(true, s0, tid, lowmask, beta, ctl->g.ev_level - 1,
                                                      ctl->g.ev_level + ctl->g.ev_range - 2, ctl->g.pbit[s0], llr_f,
                                                      single_in(gi, s0), single_out(gi, s0), Rp, xh, s_swz, alpha,
@@ -1271,7 +1282,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         for (int i = 1; i < GL; ++i) tm_fence<E>(lv[i]);
 #pragma unroll
                         for (int i = GL - 1; i >= 0; --i) {
-                            if (FIRST && i == 0 && !want_g && !PO) continue;      // stage 0 writes only the G-matrix bits
+                            if (FIRST && i == 0 && !gtest && !PO) continue;       // stage 0 writes only the G-matrix bits
                             r_layer<E, FK>(y, lv[i], i, alpha);
                             if (i > 0) {
                                 tm_st<E>(tc(colL + uint32_t((GL + i - 2) * E)), y);            // R level s0+1+i
@@ -1318,7 +1329,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 if (!FIRST) {
                     if ((rc.x >> 26) & 1) __syncwarp();
                     else sync();
-                } else if (want_g) {
+                } else if (gtest) {
                     sync();
                 }
             };
@@ -1338,24 +1349,20 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 }
             }
 
-            if (want_g) {
-                bool stop = false;
-                if (check) {
-                    if (warp == 0) {
-                        const bool gok = g_check<LOGN>(dec, xh, lane);
-                        if (lane == 0) ctl->g.g_ok = gok ? 1 : 0;
-                    }
-                    sync();
-                    stop = (!want_crc || res == 0u) && ctl->g.g_ok != 0;
+            if (gtest) {
+                if (warp == 0) {
+                    const bool gok = g_check<LOGN>(dec, xh, lane);
+                    if (lane == 0) ctl->g.g_ok = gok ? 1 : 0;
                 }
-                if (stop) {
+                sync();
+                if (ctl->g.g_ok != 0) {
                     used = it;
                     break;
                 }
                 if (it == max_iters) break;
-                // the decision words restart empty for the next iteration: their writers and readers
-                // of this one are past the barriers above; the barrier below orders the clearing
-                // before the next writes, and every read of g_ok before its next write
+                // the decision words restart empty for the next test: their writers and readers of
+                // this one are past the barriers above; the barrier below orders the clearing before
+                // the next writes, and every read of g_ok before its next write
                 for (int i = tid; i < NW; i += T) {
                     xh[i] = 0u;
                     dec[i] = 0u;
