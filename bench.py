@@ -253,6 +253,9 @@ def run_reference(args):
 
 
 MIXED_FRAMES = 1 << 20
+MIXED_PAIRS = 6          # alternating per-size / sweep timings
+# two-sided 95% Student t quantiles by degrees of freedom
+T975 = {1: 12.706, 2: 4.303, 3: 3.182, 4: 2.776, 5: 2.571, 6: 2.447, 7: 2.365, 8: 2.306, 9: 2.262, 10: 2.228}
 MIXED_LENGTHS = (128, 256, 512, 1024, 2048)
 MIXED_RATES = (0.25, 0.5, 0.75)
 
@@ -304,9 +307,9 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
     def mixed():
         md(stream)
 
-    def timed(fn, reps):
+    def timed(fn, reps, warm=0):
         with torch.cuda.stream(stream):
-            for _ in range(warmup):
+            for _ in range(warm):
                 fn()
             stream.synchronize()
             t0 = torch.cuda.Event(enable_timing=True)
@@ -316,11 +319,10 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
                 fn()
             t1.record(stream)
             stream.synchronize()
-        return t0.elapsed_time(t1) / reps
+        return t0.elapsed_time(t1) / reps if reps else 0.0
 
-    reps = max(1, min(steps, 5))
-    t_per = timed(per_size, reps)
-    t_mix = timed(mixed, reps)
+    timed(per_size, 0, warmup)
+    timed(mixed, 0, warmup)
     same = all(torch.equal(md.iters[i], decs[i].iters) and torch.equal(md.bits[i], decs[i].bits)
                for i in range(len(parts)))
     graphs = {}
@@ -331,12 +333,32 @@ def run_mixed(pcbp, inputs, dev, steps, warmup):
             stream.synchronize()
             with torch.cuda.graph(g, stream=stream):
                 fn()
-        graphs[name] = timed(g.replay, reps)
+        graphs[name] = g
+    # alternating repeats (per-size, then the sweep; plain launches and graph replays), so that
+    # clock and temperature drift falls on both sides alike; the speed-up of every pair gives a
+    # mean and a 95% interval (Student t)
+    pairs = max(MIXED_PAIRS, 2)
+    t_per, t_mix, g_per, g_mix = [], [], [], []
+    for _ in range(pairs):
+        t_per.append(timed(per_size, 1))
+        t_mix.append(timed(mixed, 1))
+        g_per.append(timed(graphs["per_size"].replay, 1))
+        g_mix.append(timed(graphs["mixed"].replay, 1))
+
+    def ratio_ci(num, den):
+        r = [a / b for a, b in zip(num, den)]
+        m = statistics.mean(r)
+        half = T975[len(r) - 1] * statistics.stdev(r) / math.sqrt(len(r))
+        return m, [m - half, m + half]
+
+    sp, sp_ci = ratio_ci(t_per, t_mix)
+    spg, spg_ci = ratio_ci(g_per, g_mix)
     return {"frames": int(MIXED_FRAMES), "classes": len(classes), "launches_per_size": len(parts),
-            "per_size_ms": t_per, "mixed_ms": t_mix, "per_size_graph_ms": graphs["per_size"],
-            "mixed_graph_ms": graphs["mixed"], "speedup": t_per / t_mix,
-            "speedup_graphs": graphs["per_size"] / graphs["mixed"],
-            "mixed_gbit_s": info_bits / (graphs["mixed"] / 1e3) / 1e9,
+            "repeats": pairs, "per_size_ms": statistics.mean(t_per), "mixed_ms": statistics.mean(t_mix),
+            "per_size_graph_ms": statistics.mean(g_per), "mixed_graph_ms": statistics.mean(g_mix),
+            "per_size_ms_runs": t_per, "mixed_ms_runs": t_mix,
+            "speedup": sp, "speedup_ci95": sp_ci, "speedup_graphs": spg, "speedup_graphs_ci95": spg_ci,
+            "mixed_gbit_s": info_bits / (statistics.mean(g_mix) / 1e3) / 1e9,
             "tuned": {str(k): v for k, v in tuned.items()}, "outputs_identical": bool(same),
             "workload": "2^20 frames, N~U{128..2048}, R~U{1/4,1/2,3/4}, Eb/N0~U[1,4] dB, PP-BP s=4 T=10, "
                         "max 300 it, CRC-8 (N<=256) / CRC-24"}
