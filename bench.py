@@ -535,13 +535,37 @@ def wbp_loss(logits, bits):
     return torch.nn.functional.binary_cross_entropy_with_logits(-logits, bits.to(logits.dtype))
 
 
+WBP_ROOF_UNIT = ("per training step: stage passes S = T n + (T-1)(n-1) (the forward's L and R sweeps; the "
+                 "backward recomputes them and runs their adjoints), N/2 processing elements each; lane-ops "
+                 "= B S (N/2) (8 forward + 8 recomputation + 16 adjoint); HBM bytes = LLRs (forward and "
+                 "every backward launch), checkpoints written (T-1) and read (T), gradient planes between "
+                 "backward launches read and written (T-1 each), logits and their gradient")
+
+
+def wbp_roofline(N, K, T, B, seconds):
+    """Achieved fraction of the derived ALU issue peak and of the measured HBM bandwidth for one
+    weighted-BP training step (algorithmic counts, WBP_ROOF_UNIT)."""
+    n = N.bit_length() - 1
+    S = T * n + (T - 1) * (n - 1)
+    lane_ops = B * S * (N // 2) * (8 + 8 + 16)
+    plane = B * (n - 1) * N * 4
+    hbm = B * N * 4 * (1 + T) + (T - 1) * plane + T * plane + 2 * (T - 1) * plane + 2 * B * K * 4
+    peaks = measured_peaks() or {}
+    alu_peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6
+    hbm_peak = peaks.get("hbm_gbs", 6800.0) * 1e9
+    fa, fh = lane_ops / seconds / alu_peak, hbm / seconds / hbm_peak
+    return {"bound": "alu" if fa >= fh else "hbm", "lane_ops": lane_ops, "tlane_op_s": lane_ops / seconds / 1e12,
+            "frac_alu": fa, "hbm_bytes": hbm, "hbm_gbs": hbm / seconds / 1e9, "frac_hbm": fh}
+
+
 def run_wbp(pcbp, inputs, dev, steps, warmup):
     """Weighted BP fwd+bwd training steps/s at batch 4096 (Eb/N0 uniform on [1, 4] dB, weights
     initialised to 0.9375, BCE on the information bits), and the largest relative error of the FP64
     kernels' gradient against FP64 central finite differences at N = 16 and 64."""
     import torch
 
-    out = {"batch": 4096, "steps_per_s": {}, "ms_per_step": {}}
+    out = {"batch": 4096, "steps_per_s": {}, "ms_per_step": {}, "roofline": {},
+           "roofline_unit": WBP_ROOF_UNIT}
     B = 4096
     for N in (256, 1024):
         K = N // 2
@@ -575,6 +599,7 @@ def run_wbp(pcbp, inputs, dev, steps, warmup):
             ms = t0.elapsed_time(t1) / reps
             out["ms_per_step"][f"N{N}_T{T}"] = ms
             out["steps_per_s"][f"N{N}_T{T}"] = 1e3 / ms
+            out["roofline"][f"N{N}_T{T}"] = wbp_roofline(N, K, T, B, ms / 1e3)
     # gradient error of the FP64 kernels against central differences
     errs = {}
     for N, T in ((16, 3), (64, 3)):
