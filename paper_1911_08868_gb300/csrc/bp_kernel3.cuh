@@ -183,6 +183,28 @@ __host__ __device__ constexpr PartitionSize max_partition(int n, int KB)
     return best;
 }
 
+// From N = 2048 on, the last group keeps its shared-memory offsets in registers instead of TMEM,
+// so that a thread's columns fit 128 (four threads per lane: two frame slots of 256 threads).
+__host__ __device__ constexpr bool tmem_last_in_regs(int n) { return n >= 11; }
+
+// TMEM columns one thread needs, the largest over every partition: the partition's interior
+// messages followed by the offsets of its register groups (the last group's too unless
+// tmem_last_in_regs).
+__host__ __device__ constexpr int max_tmem_cols(int n, int KB)
+{
+    const int E = 1 << KB;
+    const int cached_last = tmem_last_in_regs(n) ? 0 : 1;
+    PartitionSize p = partition_size(n, KB, 0, 0);
+    int best = p.cols + (p.groups - 1 + cached_last) * E;
+    for (int level = 1; level < n; ++level)
+        for (int range = 2; range <= 16 && level + range - 1 <= n; ++range) {
+            p = partition_size(n, KB, level, range);
+            const int need = p.cols + (p.groups - 1 + cached_last) * E;
+            best = need > best ? need : best;
+        }
+    return best;
+}
+
 template <int LOGN, int KB>
 struct G3 {
     static constexpr int N = 1 << LOGN;
@@ -192,22 +214,24 @@ struct G3 {
     static constexpr int NW = words_of<LOGN>();
     static constexpr int NPL = LOGN - 1;
     static constexpr PartitionSize MAXP = max_partition(LOGN, KB);
-    static constexpr int COLS = MAXP.cols;                       // interior messages
-    static constexpr int ACOL = COLS;                            // E shared-memory offsets per register group
-    static constexpr int TCOLS = ACOL + MAXP.groups * E;         // TMEM columns per thread
+    static constexpr bool LASTREG = tmem_last_in_regs(LOGN);     // the last group's offsets in registers
+    // TMEM columns per thread: a partition's interior messages, then E shared-memory offsets per
+    // register group (the last group's not when LASTREG)
+    static constexpr int TCOLS = max_tmem_cols(LOGN, KB);
     static constexpr int MAX_WARPS_TMEM = 4 * (512 / TCOLS);
     // Shared-memory planes of a frame slot, N floats each, in the swizzled
     // position order: plane p < n holds R at node level p+2 (p < n-1) and, while
     // level p+2 is interior to the group that starts at stage p, L at node level
     // p+1, the input boundary of that group (its canonical R copy is dead while
     // the partition stands: the group keeps those R messages in TMEM; plane n-1,
-    // level n+1, holds only L); plane n holds L at level 2 between two single
-    // stages; planes n+1 and n+2 hold the priors R(n+1) and the CRC
-    // contributions c_j of the positions.
-    static constexpr int NPLANES = LOGN + 3;
-    static constexpr int SPARE = LOGN;
-    static constexpr int PRIOR = LOGN + 1;
-    static constexpr int CJ = LOGN + 2;
+    // level n+1, holds only L, or L at level 2 between two single
+    // stages (the last group then has at least two stages, so plane n-1 is
+    // free); planes n and n+1 hold the priors R(n+1) and the CRC contributions
+    // c_j of the positions.
+    static constexpr int NPLANES = LOGN + 2;
+    static constexpr int SPARE = LOGN - 1;
+    static constexpr int PRIOR = LOGN;
+    static constexpr int CJ = LOGN + 1;
     static_assert(T >= 32, "every lane of a warp owns positions");
 };
 
@@ -248,12 +272,12 @@ __device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned 
 __host__ __device__ constexpr int tmem_default_kb(int logn) { return logn <= 9 ? 2 : 3; }
 
 // Largest CTA of the TMEM kernel for a length: as many frame slots as shared
-// memory and TMEM hold (N = 1024: 4 slots of 128 threads; N = 2048: one slot
+// memory and TMEM hold (N = 1024: 4 slots of 128 threads; N = 2048: 2 slots
 // of 256), at most 768 threads.
 template <int LOGN, int KB>
 __host__ __device__ constexpr int tmem_max_threads()
 {
-    return KB == 3 ? (LOGN == 10 ? 512 : (LOGN >= 11 ? 256 : 512)) : (LOGN >= 11 ? 512 : 768);
+    return KB == 3 ? 512 : (LOGN >= 11 ? 512 : 768);
 }
 
 // Per-slot control block: the stage partition plus a packed copy that the
@@ -365,8 +389,10 @@ __device__ __noinline__ void pack_groups(Ctl3<LOGN, KB>* c)
 {
     constexpr int E = 1 << KB;
     constexpr int TB = LOGN - KB;        // thread-index bits: 5 lane bits, then warp bits
-    int col = 0, acol = G3<LOGN, KB>::ACOL;
     const int ng = c->g.ng;
+    int col = 0, acol = 0;
+    for (int gi = 0; gi < ng; ++gi)       // the offsets follow this partition's interior columns
+        if (!c->g.single_[gi]) acol += group_cols(c->g.s0[gi], c->g.g[gi], false, gi == ng - 1, E);
     // position bits that receive the warp bits of the thread index (the top
     // TB - 5 bits of the deposit mask), for groups that are neither single
     // stages nor subgraph-local; ~0 otherwise
@@ -387,16 +413,18 @@ __device__ __noinline__ void pack_groups(Ctl3<LOGN, KB>* c)
         const int colL = last ? col - (gl - 1) * E : col;
         const bool wl_after = gi + 1 < ng && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi + 1);
         const bool wl_before = gi > 0 && warp_bits(gi) != ~0u && warp_bits(gi) == warp_bits(gi - 1);
+        const bool cached = !single && !(last && G3<LOGN, KB>::LASTREG);
         c->rec[gi] = make_int4(s0 | (gl << 8) | (single << 16) | (int(c->g.local[gi]) << 24) | (int(wl_after) << 25) |
                                    (int(wl_before) << 26),
                                colL,
-                               (int(c->g.contig[gi][0]) & 0xff) | ((int(c->g.contig[gi][1]) & 0xff) << 8), acol);
+                               (int(c->g.contig[gi][0]) & 0xff) | ((int(c->g.contig[gi][1]) & 0xff) << 8),
+                               cached ? acol : 0);
         c->cmask[gi] = make_uint2(c->g.cmask[gi][0], c->g.cmask[gi][1]);
         for (int cls = 0; cls < 2; ++cls)
             for (int e = 0; e < E; ++e) c->swoff[gi][cls][e] = c->g.swoff[gi][cls][e];
         if (!single) {
             col += group_cols(s0, gl, false, last, E);
-            acol += E;
+            if (cached) acol += E;
         }
     }
 }
@@ -506,8 +534,8 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
     }
     // walk the groups: this lane's group gi = lane / 2, its columns before it
     const int gi = lane >> 1, cls = lane & 1;
-    int ng = 0, my_s0 = 0, my_gl = 0, my_kind = -1, col = 0, acol = G3<LOGN, KB>::ACOL;
-    int my_col = 0, my_acol = 0, last_s0 = 0, last_gl = 0, last_kind = 0;
+    int ng = 0, my_s0 = 0, my_gl = 0, my_kind = -1, col = 0, acol = 0;
+    int my_col = 0, my_acol = 0, last_s0 = 0, last_gl = 0, last_kind = 0, last_col = 0;
     for (int sg = 0; sg < nseg; ++sg) {
         const int a = seg_a[sg], b = seg_b[sg], kind = seg_k[sg];
         const int len = b - a + 1;
@@ -519,7 +547,7 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
             if (ng == gi) {
                 my_s0 = st; my_gl = gl; my_kind = kind; my_col = col; my_acol = acol;
             }
-            last_s0 = st; last_gl = gl; last_kind = kind;
+            last_s0 = st; last_gl = gl; last_kind = kind; last_col = col;
             if (kind != 2) {
                 col += 2 * (gl - 1) * E;   // the last group's columns are counted from its R levels below
                 acol += E;
@@ -528,10 +556,13 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
             st += gl;
         }
     }
-    (void)last_s0; (void)last_gl; (void)last_kind;
+    (void)last_s0; (void)last_kind;
     const bool mine = gi < ng;
     const bool single = my_kind == 2;
     const bool last = gi == ng - 1;
+    // the offsets follow this partition's interior columns (the last group stores R levels only)
+    const int interior = last_col + (last_gl - 1) * E;
+    const bool cached = mine && !single && !(last && G3<LOGN, KB>::LASTREG);
     // register bits of (gi, cls)
     unsigned used = 0, cmask = 0;
     int contig = -1;
@@ -586,7 +617,7 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
         const int colL = last ? my_col - (my_gl - 1) * E : my_col;
         c->rec[gi] = make_int4(my_s0 | (my_gl << 8) | (int(single) << 16) | (int(my_kind != 0) << 24) |
                                    (int(wl_after) << 25) | (int(wl_before) << 26),
-                               colL, (contig & 0xff) | ((contig1 & 0xff) << 8), single ? 0 : my_acol);
+                               colL, (contig & 0xff) | ((contig1 & 0xff) << 8), cached ? interior + my_acol : 0);
         c->cmask[gi] = make_uint2(cmask, cmask1);
     }
     if (lane == 0) c->g.ng = ng;
@@ -807,7 +838,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     //   R at level s0+2+i (interior, copied at switches) d = i
     //   R at level s0+gl+1 (the next group's output)  d = gl - 1
     //   L at level s0+gl+1 (the next group's input)   d = gl
-    //   priors, CRC contributions (last group, s0 = n - gl)  d = gl + 1, gl + 2
+    //   priors, CRC contributions (last group, s0 = n - gl)  d = gl, gl + 1
     auto at = [&](int a, int floats) -> float& {
         int off = a + 4 * floats;
 #ifdef PCBP_CHECKED
@@ -849,6 +880,9 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     const bool want_crc = (S.stop_kind & 1) != 0;
 
     float L1[E];   // channel LLRs of the first group's positions
+    int ALr[E];    // the last group's offsets, when they are kept in registers (G3::LASTREG)
+#pragma unroll
+    for (int e = 0; e < E; ++e) ALr[e] = lp_off;
 
     auto group_class = [&](int meta) {
         const bool local = (meta >> 24) & 1;
@@ -917,7 +951,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #endif
 #pragma unroll
             for (int e = 0; e < E; ++e) A[e] = lp_off + 4 * (s0 * N + ph[e]);
-            tm_st_i<E>(tc(uint32_t(rc.w)), A);
+            if (Geo::LASTREG && gi == ng - 1) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) ALr[e] = A[e];
+            } else {
+                tm_st_i<E>(tc(uint32_t(rc.w)), A);
+            }
             const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {     // R level s0+2+i: plane s0+i
@@ -944,9 +983,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if ((rc.x >> 16) & 1) continue;
             if (gl < 2) continue;
             int A[E];
-            tm_ld_i<E>(tc(uint32_t(rc.w)), A);
-            tm_wait_ld();
-            tm_fence<E>(A);
+            if (Geo::LASTREG && gi == ng - 1) {
+#pragma unroll
+                for (int e = 0; e < E; ++e) A[e] = ALr[e];
+            } else {
+                tm_ld_i<E>(tc(uint32_t(rc.w)), A);
+                tm_wait_ld();
+                tm_fence<E>(A);
+            }
             const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
             #pragma unroll 1
             for (int i = 0; i < gl - 1; ++i) {
@@ -1116,7 +1160,12 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 float xL[GLL][E];
                 float x[E];
                 int cj[E];
-                tm_ld_i<E>(tc(uint32_t(rcL.w)), AL);
+                if constexpr (Geo::LASTREG) {
+#pragma unroll
+                    for (int e = 0; e < E; ++e) AL[e] = ALr[e];
+                } else {
+                    tm_ld_i<E>(tc(uint32_t(rcL.w)), AL);
+                }
 #pragma unroll
                 for (int i = 0; i < GLL - 1; ++i) tm_ld<E>(tc(colLL + uint32_t((GLL - 1 + i) * E)), rp[i]);
                 tm_wait_ld();
@@ -1124,12 +1173,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #pragma unroll
                 for (int i = 0; i < GLL - 1; ++i) tm_fence<E>(rp[i]);
                 // the last group ends at stage n-1, so it starts at s0 = n - GLL (never 0): its
-                // input, priors and CRC contributions are planes n-GLL, n+1 and n+2
+                // input, priors and CRC contributions are planes n-GLL, n and n+1
+                static_assert(Geo::PRIOR == LOGN && Geo::CJ == LOGN + 1, "plane distances below");
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     x[e] = at(AL[e], 0);
-                    pr[e] = at(AL[e], (GLL + 1) * N);
-                    cj[e] = __float_as_int(at(AL[e], (GLL + 2) * N));
+                    pr[e] = at(AL[e], GLL * N);
+                    cj[e] = __float_as_int(at(AL[e], (GLL + 1) * N));
                 }
 #pragma unroll
                 for (int i = 0; i < GLL; ++i) {
