@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 
 #include "pcbp_internal.h"
 
@@ -405,12 +406,221 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
         if (dw[i] != Real(0)) atomicAdd(P.gw + size_t(it) * n * NH * 4 + i, dw[i]);
 }
 
+// ---------------------------------------------------------------------------
+// FP32 backward for N <= 1024, one thread per processing element (tps = N/2) with the stage loops
+// unrolled for the length: every thread accumulates the weight gradient of its element (n x 4
+// values) in registers over all the frames it handles and adds it to gw once at the end, so the
+// shared memory that the accumulator takes in the kernel above holds, per frame slot, the
+// incoming gradient planes (levels 2..n, copied with cp.async when the frame starts instead of
+// read from global memory at every stage of the R-sweep adjoint) and a second copy of R(it)
+// (levels 2..n, for the adjoint of the L sweep, instead of copying the checkpoint again).  The
+// arithmetic of every stage is the kernel above's.
+// Per slot: L levels 1..n+1, R levels 2..n+1, the gradient of L at levels 1..n+1, two gradient
+// planes between R levels, G (n-1 planes), R0 (n-1 planes): (5n+2) N floats.
+template <int LOGN>
+__global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_constant__ WbpParams<float> P)
+{
+    constexpr int n = LOGN, N = 1 << LOGN, NH = N / 2;
+    constexpr int NW = N >= 32 ? N / 32 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = P.code.K;
+    const int tps = P.tps, it = P.it;
+    const bool last = it == P.T - 1;
+    uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
+    int16_t* s_info = reinterpret_cast<int16_t*>(s_frozen + NW);
+    const size_t tab = (size_t(NW) * 4 + size_t(K) * 2 + 15) & ~size_t(15);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    __syncthreads();
+    const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
+    constexpr size_t slot_reals = size_t(5 * n + 2) * N;
+    float* L = reinterpret_cast<float*>(smem + tab) + size_t(slot) * slot_reals;   // levels 1..n+1
+    float* Rt = L + (n + 1) * N;                                                   // R, levels 2..n+1
+    float* gL = Rt + n * N;                                                        // levels 1..n+1
+    float* gA = gL + (n + 1) * N;
+    float* gB = gA + N;
+    float* G = gB + N;                                                             // incoming, levels 2..n
+    float* R0 = G + (n - 1) * N;                                                   // R(it), levels 2..n
+    for (int j = tid; j < N; j += tps) Rt[(n - 1) * N + j] = prior_v<float>(s_frozen, j);
+    __shared__ long long s_frame[32];
+    const unsigned bid = 1u + unsigned(slot);
+    const float* wt = P.w + size_t(it) * n * NH * 4;
+    const bool act = tid < NH;                 // N < 64: fewer elements than a warp
+    const int q = act ? tid : 0;
+    float dwr[n][4];
+#pragma unroll
+    for (int s = 0; s < n; ++s)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) dwr[s][k] = 0.f;
+
+    while (true) {
+        if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
+        bar(bid, tps);
+        const long long f = s_frame[slot];
+        if (f >= P.B) break;
+        const float* Rp = P.ckpt + (size_t(it) * P.B + size_t(f)) * (n - 1) * N;   // R(it) before this iteration
+        copy_async(Rt, Rp, (n - 1) * N, tid, tps);
+        copy_async(R0, Rp, (n - 1) * N, tid, tps);
+        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
+        if (!last) copy_async(G, P.gin + size_t(f) * (n - 1) * N, (n - 1) * N, tid, tps);
+        for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = 0.f;
+        for (int j = tid; j < N; j += tps) gA[j] = gB[j] = 0.f;
+        copy_wait();
+        bar(bid, tps);
+        // forward recomputation of iteration it
+#pragma unroll
+        for (int s = 0; s < n; ++s) {
+            if (act) {
+                const int p = n - 1 - s;
+                const float* Ls = L + s * N;
+                const float* Rs = Rt + s * N;                                   // R(it) at level s+2
+                float* Lo = L + (s + 1) * N;
+                const int t = ins0(q, p), b = t | (1 << p);
+                const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                const float2 w2 = ld_pair(wt + (s * NH + q) * 4);
+                Lo[t] = fw(lt, radd(lb, rb), w2.x);
+                Lo[b] = radd(fw(rt, lt, w2.y), lb);
+            }
+            bar(bid, tps);
+        }
+        if (!last) {
+#pragma unroll
+            for (int s = n - 1; s >= 1; --s) {
+                if (act) {
+                    const int p = n - 1 - s;
+                    const float* Ls = L + s * N;
+                    const float* Rs = Rt + s * N;
+                    float* Ro = Rt + (s - 1) * N;
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const float2 w2 = ld_pair(wt + (s * NH + q) * 4 + 2);
+                    Ro[t] = fw(rt, radd(lb, rb), w2.x);
+                    Ro[b] = radd(fw(rt, lt, w2.y), rb);
+                }
+                bar(bid, tps);
+            }
+        } else {
+            for (int k = tid; k < K; k += tps) gL[n * N + s_info[k]] = P.glogits[size_t(f) * K + k];
+            bar(bid, tps);
+        }
+        // adjoint of the R sweep: stage s makes R level s+1 from R level s+2 and L level s+1
+        if (!last) {
+#pragma unroll
+            for (int s = 1; s <= n - 1; ++s) {
+                if (act) {
+                    const int p = n - 1 - s;
+                    const float* gis = G + (s - 1) * N;
+                    const float* Rs = Rt + s * N;                               // R level s+2
+                    const float* Ls = L + s * N;
+                    float* gLs = gL + s * N;
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const float gt = radd(gis[t], gA[t]);                        // gradient of R level s+1
+                    const float gb = radd(gis[b], gA[b]);
+                    const float a = Rs[t], rb = Rs[b];
+                    const float lt = Ls[t], lb = Ls[b];
+                    float ct = 0.f, cb = 0.f;
+                    if (gt != 0.f || gb != 0.f) {
+                        const float2 w2 = ld_pair(wt + (s * NH + q) * 4 + 2);   // w[2], w[3]
+                        if (gt != 0.f) {                                         // R_out1 = f(a, lb + rb; w2)
+                            const float c = radd(lb, rb);
+                            const bool amin = fabsf(a) <= fabsf(c);
+                            const float m = amin ? fabsf(a) : fabsf(c);
+                            dwr[s][2] = radd(dwr[s][2], rmul(gt, sgn(a) * sgn(c) * m));
+                            if (amin) {
+                                ct = radd(ct, rmul(rmul(gt, w2.x), sgn(c)));
+                            } else {
+                                const float gc = rmul(rmul(gt, w2.x), sgn(a));
+                                gLs[b] = radd(gLs[b], gc);
+                                cb = radd(cb, gc);
+                            }
+                        }
+                        if (gb != 0.f) {                                         // R_out2 = f(a, lt; w3) + rb
+                            cb = radd(cb, gb);
+                            const bool amin = fabsf(a) <= fabsf(lt);
+                            const float m = amin ? fabsf(a) : fabsf(lt);
+                            dwr[s][3] = radd(dwr[s][3], rmul(gb, sgn(a) * sgn(lt) * m));
+                            if (amin) ct = radd(ct, rmul(rmul(gb, w2.y), sgn(lt)));
+                            else gLs[t] = radd(gLs[t], rmul(rmul(gb, w2.y), sgn(a)));
+                        }
+                    }
+                    gB[t] = ct;                                                  // contributions to R level s+2
+                    gB[b] = cb;
+                }
+                bar(bid, tps);
+                float* tmp = gA; gA = gB; gB = tmp;
+            }
+        }
+        // adjoint of the L sweep: stage s makes L level s+2 from L level s+1 and R(it) level s+2
+        float* gout = P.gout + size_t(f) * (n - 1) * N;
+#pragma unroll
+        for (int s = n - 1; s >= 0; --s) {
+            if (act) {
+                const int p = n - 1 - s;
+                const float* Ls = L + s * N;
+                const float* Rs = s < n - 1 ? R0 + s * N : Rt + (n - 1) * N;    // R(it) level s+2 (n+1: priors)
+                float* gLs = gL + s * N;
+                const float* gLo = gL + (s + 1) * N;
+                float* gos = gout + size_t(s) * N;
+                const int t = ins0(q, p), b = t | (1 << p);
+                const float gt = gLo[t], gb = gLo[b];
+                float gRt = 0.f, gRb = 0.f;
+                float gat = gLs[t], gab = gLs[b];
+                if (gt != 0.f || gb != 0.f) {
+                    const float a = Ls[t], lb = Ls[b];
+                    const float rt = Rs[t], rb = Rs[b];
+                    const float2 w2 = ld_pair(wt + (s * NH + q) * 4);           // w[0], w[1]
+                    if (gt != 0.f) {                                             // L_out1 = f(a, lb + rb; w0)
+                        const float c = radd(lb, rb);
+                        const bool amin = fabsf(a) <= fabsf(c);
+                        const float m = amin ? fabsf(a) : fabsf(c);
+                        dwr[s][0] = radd(dwr[s][0], rmul(gt, sgn(a) * sgn(c) * m));
+                        if (amin) {
+                            gat = radd(gat, rmul(rmul(gt, w2.x), sgn(c)));
+                        } else {
+                            const float gc = rmul(rmul(gt, w2.x), sgn(a));
+                            gab = radd(gab, gc);
+                            gRb = radd(gRb, gc);
+                        }
+                    }
+                    if (gb != 0.f) {                                             // L_out2 = f(rt, a; w1) + lb
+                        gab = radd(gab, gb);
+                        const bool rmin = fabsf(rt) <= fabsf(a);
+                        const float m = rmin ? fabsf(rt) : fabsf(a);
+                        dwr[s][1] = radd(dwr[s][1], rmul(gb, sgn(rt) * sgn(a) * m));
+                        if (rmin) gRt = radd(gRt, rmul(rmul(gb, w2.y), sgn(a)));
+                        else gat = radd(gat, rmul(rmul(gb, w2.y), sgn(rt)));
+                    }
+                }
+                gLs[t] = gat;
+                gLs[b] = gab;
+                if (s < n - 1) {
+                    gos[t] = gRt;
+                    gos[b] = gRb;
+                }
+            }
+            bar(bid, tps);
+        }
+        if (P.gllr)
+            for (int j = tid; j < N; j += tps) P.gllr[size_t(f) * N + j] = radd(P.gllr[size_t(f) * N + j], gL[j]);
+        bar(bid, tps);
+    }
+    if (act) {
+        float* g = P.gw + size_t(it) * n * NH * 4 + size_t(q) * 4;
+#pragma unroll
+        for (int s = 0; s < n; ++s)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                if (dwr[s][k] != 0.f) atomicAdd(g + size_t(s) * NH * 4 + k, dwr[s][k]);
+    }
+}
+
 struct Geo {
     int tps, slots, grid;
     size_t smem;
 };
 
-int wbp_geometry(const pc_code* c, int64_t B, size_t real_bytes, bool backward, Geo* g)
+// reg: the FP32 backward with the weight gradient in registers (wbp_backward_reg_kernel).
+int wbp_geometry(const pc_code* c, int64_t B, size_t real_bytes, bool backward, Geo* g, bool reg = false)
 {
     int dev = 0, sms = 0, optin = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return PC_ECUDA;
@@ -420,12 +630,13 @@ int wbp_geometry(const pc_code* c, int64_t B, size_t real_bytes, bool backward, 
     const int N = c->N, n = c->n;
     const int NW = N >= 32 ? N / 32 : 1;
     const size_t tab = (size_t(NW) * 4 + size_t(c->K) * 2 + 15) & ~size_t(15);
-    const size_t fixed = tab + (backward ? ((size_t(n) * (N / 2) * 4 * real_bytes + 15) & ~size_t(15)) : 0);
-    const size_t slot = (backward ? size_t(3 * n + 4) : size_t(2 * n + 1)) * N * real_bytes;
+    const size_t fixed =
+        tab + (backward && !reg ? ((size_t(n) * (N / 2) * 4 * real_bytes + 15) & ~size_t(15)) : 0);
+    const size_t slot = (reg ? size_t(5 * n + 2) : (backward ? size_t(3 * n + 4) : size_t(2 * n + 1))) * N * real_bytes;
     g->tps = std::max(32, std::min(512, N / 2));
     if (fixed + slot > size_t(optin)) return PC_EUNSUPPORTED;
     int slots = int((size_t(optin) - fixed) / slot);
-    slots = std::max(1, std::min({slots, 15, 1024 / g->tps}));
+    slots = std::max(1, std::min({slots, 15, (reg ? 512 : 1024) / g->tps}));
     g->slots = slots;
     g->smem = fixed + size_t(slots) * slot;
     g->grid = int(std::min<int64_t>(int64_t(sms), (B + slots - 1) / slots));
@@ -477,6 +688,31 @@ int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, in
     return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
 }
 
+// The register-accumulating FP32 backward, instantiated for n = 3..10.
+cudaError_t launch_backward_reg(int n, const WbpParams<float>& P, const Geo& g, cudaStream_t st)
+{
+#define PCBP_WBP_REG(k)                                                                                      \
+    case k: {                                                                                                \
+        cudaError_t e = cudaFuncSetAttribute(wbp_backward_reg_kernel<k>,                                     \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));      \
+        if (e != cudaSuccess) return e;                                                                      \
+        wbp_backward_reg_kernel<k><<<g.grid, g.slots * g.tps, g.smem, st>>>(P);                              \
+        return cudaGetLastError();                                                                           \
+    }
+    switch (n) {
+        PCBP_WBP_REG(3)
+        PCBP_WBP_REG(4)
+        PCBP_WBP_REG(5)
+        PCBP_WBP_REG(6)
+        PCBP_WBP_REG(7)
+        PCBP_WBP_REG(8)
+        PCBP_WBP_REG(9)
+        PCBP_WBP_REG(10)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PCBP_WBP_REG
+}
+
 template <typename Real>
 int backward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, int64_t B, const Real* ckpt,
                   const Real* glogits, Real* gw, Real* gllr, void* ws, void* stream)
@@ -486,8 +722,10 @@ int backward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, i
     if (B == 0) return PC_OK;
     if (!llr || !w || !ckpt || !glogits || !gw || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
     if (reinterpret_cast<uintptr_t>(w) & (2 * sizeof(Real) - 1)) return PC_EINVAL;   // weights are read in pairs
+    // FP32 up to N = 1024: the weight gradient in registers, incoming gradients staged per frame
+    const bool reg = std::is_same<Real, float>::value && c->n <= 10;
     Geo g;
-    rc = wbp_geometry(c, B, sizeof(Real), true, &g);
+    rc = wbp_geometry(c, B, sizeof(Real), true, &g, reg);
     if (rc != PC_OK) return rc;
     std::unique_ptr<WbpParams<Real>> P(new WbpParams<Real>);
     std::memset(P.get(), 0, sizeof(WbpParams<Real>));
@@ -507,14 +745,20 @@ int backward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, i
     state[1] = state[0] + size_t(B) * size_t(c->n - 1) * size_t(c->N);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (gllr && cudaMemsetAsync(gllr, 0, size_t(B) * c->N * sizeof(Real), st) != cudaSuccess) return PC_ECUDA;
-    if (cudaFuncSetAttribute(wbp_backward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
-        cudaSuccess)
+    if (!reg && cudaFuncSetAttribute(wbp_backward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      int(g.smem)) != cudaSuccess)
         return PC_ECUDA;
     for (int it = T - 1; it >= 0; --it) {
         P->it = it;
         P->gin = state[(T - 1 - it) & 1];      // written by the launch of iteration it+1 (unused at it = T-1)
         P->gout = state[(T - it) & 1];
         if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
+        if constexpr (std::is_same<Real, float>::value) {
+            if (reg) {
+                if (launch_backward_reg(c->n, *P, g, st) != cudaSuccess) return PC_ECUDA;
+                continue;
+            }
+        }
         wbp_backward_kernel<Real><<<g.grid, g.slots * g.tps, g.smem, st>>>(*P);
         if (cudaGetLastError() != cudaSuccess) return PC_ECUDA;
     }

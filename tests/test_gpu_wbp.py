@@ -76,13 +76,15 @@ def test_gradcheck_fp64_kernels(pcbp, oracle, N, K, T, B):
     assert torch.autograd.gradcheck(loss, (l, ww), eps=1e-7, atol=1e-6, rtol=1e-5)
 
 
-def test_fp32_kernels_match_fp32_reference(pcbp, oracle):
+@pytest.mark.parametrize("case", [(32, 16, 6, 40), (256, 128, 10, 64), (1024, 512, 6, 24)],
+                         ids=lambda c: f"N{c[0]}")
+def test_fp32_kernels_match_fp32_reference(pcbp, oracle, case):
     """FP32 kernels against the same reference evaluated in FP32: identical
     operation order, so the logits match exactly and the gradients differ
     only in summation order.  Against FP64, min-sum near-ties resolve
     differently in a few processing elements (the gradient is rerouted), so
     that comparison is loose."""
-    N, K, T, B = 256, 128, 10, 64
+    N, K, T, B = case
     fr, pay, llr, w = setup(oracle, N, K, B, T, seed=99)
     code = pcbp.pc_construct(N, K)
     r32l, r32w, r32g = reference(fr, pay, llr.float(), w.float(), T)
@@ -90,9 +92,10 @@ def test_fp32_kernels_match_fp32_reference(pcbp, oracle):
     assert torch.equal(gl, r32l.double())
     assert (gw - r32w.double()).norm() / r32w.double().norm() < 1e-4
     assert (gg - r32g.double()).norm() / r32g.double().norm() < 1e-4
-    r64l, r64w, _ = reference(fr, pay, llr, w, T)
-    assert (gl - r64l).abs().max() / r64l.abs().max() < 1e-3
-    assert (gw - r64w).norm() / r64w.norm() < 2e-2
+    if N == 256:
+        r64l, r64w, _ = reference(fr, pay, llr, w, T)
+        assert (gl - r64l).abs().max() / r64l.abs().max() < 1e-3
+        assert (gw - r64w).norm() / r64w.norm() < 2e-2
 
 
 def test_training_lowers_the_loss(pcbp, oracle):
