@@ -204,6 +204,90 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
 }
 
 // ---------------------------------------------------------------------------
+// FP32 forward for N <= 1024 with the stage loops unrolled for the length: one thread per
+// processing element (tps = N/2), so every index and plane offset of a stage is a compile-time
+// shift or constant.  Same planes and arithmetic as wbp_forward_kernel.
+template <int LOGN>
+__global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_constant__ WbpParams<float> P)
+{
+    constexpr int n = LOGN, N = 1 << LOGN, NH = N / 2;
+    constexpr int NW = N >= 32 ? N / 32 : 1;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int K = P.code.K;
+    const int tps = P.tps;
+    uint32_t* s_frozen = reinterpret_cast<uint32_t*>(smem);
+    int16_t* s_info = reinterpret_cast<int16_t*>(s_frozen + NW);
+    for (int i = threadIdx.x; i < NW; i += blockDim.x) s_frozen[i] = P.code.frozen[i];
+    for (int i = threadIdx.x; i < K; i += blockDim.x) s_info[i] = P.code.info_idx[i];
+    __syncthreads();
+    const size_t tab = (size_t(NW) * 4 + size_t(K) * 2 + 15) & ~size_t(15);
+    const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
+    float* L = reinterpret_cast<float*>(smem + tab + size_t(slot) * size_t(2 * n + 1) * N * sizeof(float));
+    float* R = L + (n + 1) * N;                   // plane l-2 = level l, 2 <= l <= n+1
+    for (int j = tid; j < N; j += tps) R[(n - 1) * N + j] = prior_v<float>(s_frozen, j);
+    __shared__ long long s_frame[32];
+    const unsigned bid = 1u + unsigned(slot);
+    const bool act = tid < NH;                    // N < 64: fewer elements than a warp
+    const int q = act ? tid : 0;
+
+    while (true) {
+        if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
+        bar(bid, tps);
+        const long long f = s_frame[slot];
+        if (f >= P.B) break;
+        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
+        for (int j = tid; j < (n - 1) * N; j += tps) R[j] = 0.f;
+        if (P.ckpt)
+            for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = 0.f;
+        copy_wait();
+        bar(bid, tps);
+        for (int it = 0; it < P.T; ++it) {
+            const float* wq = P.w + size_t(it) * n * NH * 4 + size_t(q) * 4;
+#pragma unroll
+            for (int s = 0; s < n; ++s) {
+                if (act) {
+                    const int p = n - 1 - s;
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const float* Ls = L + s * N;
+                    const float* Rs = R + s * N;           // level s+2
+                    float* Lo = L + (s + 1) * N;
+                    const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const float2 w2 = ld_pair(wq + s * NH * 4);   // k = 0, 1
+                    Lo[t] = fw(lt, radd(lb, rb), w2.x);
+                    Lo[b] = radd(fw(rt, lt, w2.y), lb);
+                }
+                bar(bid, tps);
+            }
+            if (it == P.T - 1) break;
+#pragma unroll
+            for (int s = n - 1; s >= 1; --s) {
+                if (act) {
+                    const int p = n - 1 - s;
+                    const int t = ins0(q, p), b = t | (1 << p);
+                    const float* Ls = L + s * N;
+                    const float* Rs = R + s * N;           // level s+2
+                    float* Ro = R + (s - 1) * N;           // level s+1
+                    const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
+                    const float2 w2 = ld_pair(wq + s * NH * 4 + 2);   // k = 2, 3
+                    Ro[t] = fw(rt, radd(lb, rb), w2.x);
+                    Ro[b] = radd(fw(rt, lt, w2.y), rb);
+                }
+                bar(bid, tps);
+            }
+            if (P.ckpt) {
+                // no barrier after the copy: the R planes are next written by the R sweep of
+                // the next iteration, n slot barriers later
+                float4* dst = reinterpret_cast<float4*>(P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N);
+                const float4* src = reinterpret_cast<const float4*>(R);
+                for (int j = tid; j < (n - 1) * N / 4; j += tps) dst[j] = src[j];
+            }
+        }
+        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[n * N + s_info[k]];
+        bar(bid, tps);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Shared memory per frame slot: L at levels 1..n+1, R at levels 2..n+1 (level
 // n+1: the priors, written once per CTA), the gradient of L at levels 1..n+1
 // and two planes for the gradient flowing between R levels.  The R planes hold
@@ -656,36 +740,28 @@ size_t workspace_bytes(const pc_code* c, int64_t B, size_t real_bytes)
     return 256 + 2 * size_t(B) * size_t(c->n - 1) * size_t(c->N) * real_bytes;
 }
 
-template <typename Real>
-int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, int64_t B, Real* logits, Real* ckpt,
-                 void* ws, void* stream)
+// The unrolled FP32 forward, instantiated for n = 4..10.
+cudaError_t launch_forward_reg(int n, const WbpParams<float>& P, const Geo& g, cudaStream_t st)
 {
-    int rc = validate_common(c, T, B);
-    if (rc != PC_OK) return rc;
-    if (B == 0) return PC_OK;
-    if (!llr || !w || !logits || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
-    if (reinterpret_cast<uintptr_t>(w) & (2 * sizeof(Real) - 1)) return PC_EINVAL;   // weights are read in pairs
-    Geo g;
-    rc = wbp_geometry(c, B, sizeof(Real), false, &g);
-    if (rc != PC_OK) return rc;
-    std::unique_ptr<WbpParams<Real>> P(new WbpParams<Real>);
-    std::memset(P.get(), 0, sizeof(WbpParams<Real>));
-    build_dev_code(c, &P->code);
-    P->llr = llr;
-    P->w = w;
-    P->logits = logits;
-    P->ckpt = ckpt;
-    P->counter = static_cast<unsigned long long*>(ws);
-    P->B = B;
-    P->T = T;
-    P->tps = g.tps;
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
-    if (cudaFuncSetAttribute(wbp_forward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
-        cudaSuccess)
-        return PC_ECUDA;
-    wbp_forward_kernel<Real><<<g.grid, g.slots * g.tps, g.smem, st>>>(*P);
-    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
+#define PCBP_WBP_FWD(k)                                                                                      \
+    case k: {                                                                                                \
+        cudaError_t e = cudaFuncSetAttribute(wbp_forward_reg_kernel<k>,                                      \
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem));      \
+        if (e != cudaSuccess) return e;                                                                      \
+        wbp_forward_reg_kernel<k><<<g.grid, g.slots * g.tps, g.smem, st>>>(P);                               \
+        return cudaGetLastError();                                                                           \
+    }
+    switch (n) {
+        PCBP_WBP_FWD(4)
+        PCBP_WBP_FWD(5)
+        PCBP_WBP_FWD(6)
+        PCBP_WBP_FWD(7)
+        PCBP_WBP_FWD(8)
+        PCBP_WBP_FWD(9)
+        PCBP_WBP_FWD(10)
+        default: return cudaErrorInvalidValue;
+    }
+#undef PCBP_WBP_FWD
 }
 
 // The register-accumulating FP32 backward, instantiated for n = 3..10.
@@ -711,6 +787,44 @@ cudaError_t launch_backward_reg(int n, const WbpParams<float>& P, const Geo& g, 
         default: return cudaErrorInvalidValue;
     }
 #undef PCBP_WBP_REG
+}
+
+template <typename Real>
+int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, int64_t B, Real* logits, Real* ckpt,
+                 void* ws, void* stream)
+{
+    int rc = validate_common(c, T, B);
+    if (rc != PC_OK) return rc;
+    if (B == 0) return PC_OK;
+    if (!llr || !w || !logits || !ws || (reinterpret_cast<uintptr_t>(ws) & 255u)) return PC_EINVAL;
+    if (reinterpret_cast<uintptr_t>(w) & (2 * sizeof(Real) - 1)) return PC_EINVAL;   // weights are read in pairs
+    Geo g;
+    rc = wbp_geometry(c, B, sizeof(Real), false, &g);
+    if (rc != PC_OK) return rc;
+    std::unique_ptr<WbpParams<Real>> P(new WbpParams<Real>);
+    std::memset(P.get(), 0, sizeof(WbpParams<Real>));
+    build_dev_code(c, &P->code);
+    P->llr = llr;
+    P->w = w;
+    P->logits = logits;
+    P->ckpt = ckpt;
+    P->counter = static_cast<unsigned long long*>(ws);
+    P->B = B;
+    P->T = T;
+    P->tps = g.tps;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
+    if constexpr (std::is_same<Real, float>::value) {
+        // FP32 up to N = 1024 (from N = 16, with the checkpoints 16-byte aligned: their rows of
+        // (n-1) N floats are copied as float4)
+        if (c->n >= 4 && c->n <= 10 && (reinterpret_cast<uintptr_t>(ckpt) & 15u) == 0)
+            return launch_forward_reg(c->n, *P, g, st) == cudaSuccess ? PC_OK : PC_ECUDA;
+    }
+    if (cudaFuncSetAttribute(wbp_forward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
+        cudaSuccess)
+        return PC_ECUDA;
+    wbp_forward_kernel<Real><<<g.grid, g.slots * g.tps, g.smem, st>>>(*P);
+    return cudaGetLastError() == cudaSuccess ? PC_OK : PC_ECUDA;
 }
 
 template <typename Real>
