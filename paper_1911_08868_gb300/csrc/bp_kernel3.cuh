@@ -903,8 +903,9 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     };
 
     // A new frame on the partition the TMEM caches already describe: zero
-    // interior R messages, channel LLRs of group 0's positions.
-    auto restart_partition = [&](const float* llr_f) {
+    // interior R messages, channel LLRs of group 0's positions (from llr_src,
+    // in natural position order).
+    auto restart_partition = [&](const float* llr_src) {
         const int ng = ctl->g.ng;
         float z[E];
 #pragma unroll
@@ -923,7 +924,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 tm_wait_ld();
                 tm_fence<E>(A);
 #pragma unroll
-                for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + pos_of(A[e], 0));
+                for (int e = 0; e < E; ++e) L1[e] = llr_src[pos_of(A[e], 0)];
             }
         }
         tm_wait_st();
@@ -931,8 +932,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 
     // After a new partition: cache the register groups' offsets in TMEM, move
     // the interior R messages from the canonical planes to TMEM, load the
-    // channel LLRs of the first group.
-    auto enter_partition = [&](const float* llr_f) {
+    // channel LLRs of the first group (from llr_src, in natural position order).
+    auto enter_partition = [&](const float* llr_src) {
         const int ng = ctl->g.ng;
         #pragma unroll 1
         for (int gi = 0; gi < ng; ++gi) {
@@ -967,7 +968,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             }
             if (gi == 0) {
 #pragma unroll
-                for (int e = 0; e < E; ++e) L1[e] = __ldcs(llr_f + sw(ph[e]));
+                for (int e = 0; e < E; ++e) L1[e] = llr_src[sw(ph[e])];
             }
         }
         tm_wait_st();
@@ -1032,6 +1033,18 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         const long long f = ctl->g.frame;
         if (f >= J.B) break;
         const float* llr_f = J.llr + size_t(f) * N;
+        // a1: the frame's channel LLRs stream into plane n-1 (free between frames) as 16-byte
+        // asynchronous copies, while the planes are cleared; the first group's threads then read
+        // their positions from shared memory
+        float* s_llr = Rp + Geo::SPARE * N;
+        {
+            const uint32_t d = uint32_t(__cvta_generic_to_shared(s_llr));
+            const size_t g = size_t(__cvta_generic_to_global(llr_f));
+            for (int i = tid; i < N / 4; i += T)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16u * uint32_t(i)),
+                             "l"(g + 16u * size_t(i))
+                             : "memory");
+        }
 
         for (int i = tid; i < NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = tid; i < NW; i += T) {
@@ -1050,15 +1063,13 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             for (int i = tid; i < int(sizeof(Ctl) / 16); i += T)
                 reinterpret_cast<int4*>(ctl)[i] = reinterpret_cast<const int4*>(tmpl)[i];
         }
+        asm volatile("cp.async.wait_all;" ::: "memory");
         sync();
-        if (fresh) {
-            restart_partition(llr_f);
-        } else {
-            // enter_partition reads the interior R planes, which the first L sweep overwrites
-            // with boundary L messages: every thread's reads come first
-            enter_partition(llr_f);
-            sync();
-        }
+        // both read the staged LLRs and (enter_partition) the interior R planes, which the first
+        // L sweep overwrites with boundary L messages: every thread's reads come first
+        if (fresh) restart_partition(s_llr);
+        else enter_partition(s_llr);
+        sync();
         fresh = true;
 
         int next_reset = S.mode == 1 ? S.T0 : (S.mode == 2 ? S.it_reset_full : 0);
@@ -1465,7 +1476,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     next_reset = it + ctl->g.next_inc;
                     ++kev;
                     sync();
-                    enter_partition(llr_f);   // interior R of the new partition to TMEM
+                    enter_partition(llr_f);   // interior R of the new partition to TMEM, LLRs from global memory
                     sync();
                 }
             }
