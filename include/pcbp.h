@@ -132,7 +132,7 @@ int bp_decode_workspace_size(const pc_code* code, int64_t B, size_t* bytes);
  * Messages are FP32; every FP32 operation is rounded as written (no fused
  * multiply-add), so results are reproducible bit for bit.  N >= 128 runs the
  * kernel that keeps each stage group's interior messages in tensor memory
- * (groups of 2 stages up to N = 512, of 3 from 1024), smaller N the shared-memory
+ * (groups of 2 stages up to N = 256, of 3 from 512), smaller N the shared-memory
  * stage-grouped kernel (the environment variable
  * PCBP_DECODER=grouped selects the latter for every N; the outputs are the
  * same).  The frames of a call share a persistent grid: each CTA holds one
@@ -301,7 +301,7 @@ int pc_build_info(int32_t* flags);
 
 /* Threads per frame of a decoder kernel for this code (kernel 0: the kernel
  * with TMEM-resident stage groups, N = 128..2048, groups of 2 stages up to
- * N = 512 and of 3 from N = 1024, so N/4 or N/8; kernel 1: the shared-memory
+ * N = 256 and of 3 from N = 512, so N/4 or N/8; kernel 1: the shared-memory
  * stage-grouped kernel, max(32, N/4)), the value pc_batch.threads_per_frame
  * takes to select it; where the two are equal the TMEM kernel runs unless
  * PCBP_DECODER=grouped.  Host only, no device call.  No counterpart in the

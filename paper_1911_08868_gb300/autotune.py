@@ -5,7 +5,7 @@ For each length it decodes a synthetic batch (rate 1/2, BPSK/AWGN at the given
 Eb/N0, the given schedule) with every candidate shape through a single-batch
 MixedDecoder, times the launches with CUDA events and keeps the fastest.
 Threads per frame: the counts bp_kernel_threads reports for the two kernels
-(TMEM-resident stage groups: N/4 up to N = 512, N/8 from 1024; shared-memory
+(TMEM-resident stage groups: N/4 up to N = 256, N/8 from 512; shared-memory
 groups: max(32, N/4); where they coincide the library runs the TMEM kernel).  Results are cached per GPU
 name, library build and schedule in a JSON file ($PCBP_TUNE_CACHE, default ~/.cache/pcbp_tune.json).
 """

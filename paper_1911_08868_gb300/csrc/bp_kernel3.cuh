@@ -183,6 +183,23 @@ __host__ __device__ constexpr PartitionSize max_partition(int n, int KB)
     return best;
 }
 
+// Whether plane n-1 can hold L at level 2 between two single stages: single stages exist only for
+// events narrower than a group (m = level + range - 1 < KB, so at level 1 after 0 or more stages),
+// and plane n-1 is free in those partitions when their last group has at least two stages (it is
+// the input plane of a one-stage last group).  The last segment puts its short group last.
+__host__ __device__ constexpr bool spare_is_plane_n_minus_1(int n, int KB)
+{
+    for (int level = 1; level < n; ++level)
+        for (int range = 2; range <= 16 && level + range - 1 <= n; ++range) {
+            const int hi = level + range - 2, m = hi + 1;
+            if (m >= KB || hi + 1 > n - 1) continue;
+            const int len = n - 1 - hi;            // the stages after the single ones
+            const int last = len % KB == 0 ? KB : len % KB;
+            if (last < 2) return false;
+        }
+    return true;
+}
+
 // From N = 2048 on, the last group keeps its shared-memory offsets in registers instead of TMEM,
 // so that a thread's columns fit 128 (four threads per lane: two frame slots of 256 threads).
 __host__ __device__ constexpr bool tmem_last_in_regs(int n) { return n >= 11; }
@@ -225,11 +242,13 @@ struct G3 {
     // p+1, the input boundary of that group (its canonical R copy is dead while
     // the partition stands: the group keeps those R messages in TMEM; plane n-1,
     // level n+1, holds only L, or L at level 2 between two single
-    // stages (the last group then has at least two stages, so plane n-1 is
-    // free); planes n and n+1 hold the priors R(n+1) and the CRC contributions
-    // c_j of the positions.
-    static constexpr int NPLANES = LOGN + 2;
-    static constexpr int SPARE = LOGN - 1;
+    // stages where the last group then has at least two stages, so plane n-1
+    // is free (else plane n+2); planes n and n+1 hold the priors R(n+1) and the
+    // CRC contributions c_j of the positions.  The spare plane also receives a
+    // frame's channel LLRs as the frame starts.
+    static constexpr bool SPARE_SHARED = spare_is_plane_n_minus_1(LOGN, KB);
+    static constexpr int NPLANES = SPARE_SHARED ? LOGN + 2 : LOGN + 3;
+    static constexpr int SPARE = SPARE_SHARED ? LOGN - 1 : LOGN + 2;
     static constexpr int PRIOR = LOGN;
     static constexpr int CJ = LOGN + 1;
     static_assert(T >= 32, "every lane of a warp owns positions");
@@ -265,11 +284,11 @@ __device__ __forceinline__ void load_code_tables3(const DevCode& code, unsigned 
     for (int i = threadIdx.x; i < kSwzTableBytes; i += blockDim.x) s_swz[i] = swz_row(i);
 }
 
-// Stages per group of the TMEM kernel for a length: 2 up to N = 512 (twice the
-// warps per frame, faster there: N = 256 2.15 against 2.84 ms, N = 512 6.87
-// against 7.25 ms on 65,536 PP-BP frames at 2.5 dB), 3 from N = 1024 (N = 1024
-// 8.00 against 9.51 ms, N = 2048 16.9 against 20.4 ms).
-__host__ __device__ constexpr int tmem_default_kb(int logn) { return logn <= 9 ? 2 : 3; }
+// Stages per group of the TMEM kernel for a length: 2 up to N = 256 (twice the
+// warps per frame, faster there: N = 256 2.13 against 2.30 ms on 65,536 PP-BP
+// frames at 2.5 dB), 3 from N = 512 (N = 512 5.81 against 7.06 ms, N = 1024
+// 6.93 against 9.5 ms).
+__host__ __device__ constexpr int tmem_default_kb(int logn) { return logn <= 8 ? 2 : 3; }
 
 // Largest CTA of the TMEM kernel for a length: as many frame slots as shared
 // memory and TMEM hold (N = 1024: 4 slots of 128 threads; N = 2048: 2 slots

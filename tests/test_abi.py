@@ -267,9 +267,9 @@ def test_slot_limit_validates_on_the_host(pcbp):
 
 def test_kernel_threads_is_a_host_query(pcbp):
     """Threads per frame of each decoder kernel, without a device: the TMEM kernel takes N/4 up
-    to N = 512 and N/8 from 1024 and has no build below N = 128; the shared-memory kernel takes
+    to N = 256 and N/8 from 512 and has no build below N = 128; the shared-memory kernel takes
     max(32, N/4)."""
-    want = {64: (None, 32), 128: (32, 32), 256: (64, 64), 512: (128, 128), 1024: (128, 256), 2048: (256, 512)}
+    want = {64: (None, 32), 128: (32, 32), 256: (64, 64), 512: (64, 128), 1024: (128, 256), 2048: (256, 512)}
     for N, (t0, t1) in want.items():
         code = pcbp.pc_construct(N, N // 2)
         assert pcbp.bp_kernel_threads(code, 0) == t0, N
