@@ -13,19 +13,30 @@
 // s0+1 for them: these boundary levels stay in shared memory.  The levels
 // inside the group are produced and consumed by the same thread on the same
 // positions while the partition stays:
-//   L at levels s0+1 .. s0+gl    written by the L sweep, read by the R sweep
-//                                (level 1 is the channel LLRs, in registers;
-//                                the last group keeps its L in registers),
+//   L at levels s0+2 .. s0+gl    written by the L sweep, read by the R sweep
+//                                (L at level s0+1 is read again from its
+//                                boundary plane; the last group keeps its L
+//                                in registers),
 //   R at levels s0+2 .. s0+gl    written by the R sweep, read by the next
 //                                L sweep.
 // Each thread keeps these E = 2^KB values per level in its own TMEM lane
 // (tcgen05.st/ld, 32x32b shape: the warp's quarter of the 128 lanes, one
-// column per value), a warp's columns at bank (warp / 4) * TCOLS.  It also
-// caches there, per group, the shared-memory offsets of its E positions and,
-// for the last group, their priors and CRC contributions: these depend only
-// on the partition.  Only the thread that wrote a value reads it back, so no
-// fence orders TMEM across threads; tcgen05.wait::st orders a thread's stores
-// before its next loads.
+// column per value), a warp's columns at bank (warp / 4) * TCOLS, followed by
+// the shared-memory offsets of its E positions per register group (the last
+// group's in registers from N = 2048 on): these depend only on the partition.
+// Only the thread that wrote a value reads it back, so no fence orders TMEM
+// across threads; tcgen05.wait::st orders a thread's stores before its next
+// loads.
+//
+// Shared-memory planes (G3): R at every level 2..n in canonical planes; the
+// boundary L a group reads lives in the plane of R at the level above it,
+// which is interior to that group (its R messages are in TMEM while the
+// partition stands), so all planes a group touches are at compile-time
+// distances from its cached offsets; at a switch the interior R messages go
+// back to those planes, are reset as Sec. III says and are read into TMEM
+// for the new partition.  Per slot also: the priors and CRC contributions of
+// the positions, and a spare plane (the channel LLRs as a frame starts; L at
+// level 2 between two single stages).
 //
 // Fewer barriers.  The CRC residue of the decisions is linear in them: each
 // thread XORs the cached contributions c_j (x^(K-1-k) mod g for the
@@ -34,9 +45,11 @@
 // group's R sweep runs before the stop test (wasted only in a frame's final
 // iteration), so a single barrier publishes both the residue and that
 // group's boundary R.  Decision words are written only when the frame stops
-// or runs out of iterations (every iteration when the G-matrix test needs
-// them).  Group 0's R sweep writes nothing other threads read unless the
-// G-matrix test is on, so no barrier follows it then.  Where two neighbouring
+// or runs out of iterations, and on the iterations that run the G-matrix
+// test (from stop_from on; with the combined stop only where the CRC residue
+// is zero, since the frame goes on otherwise).  Group 0's R sweep writes
+// nothing other threads read unless the G-matrix test runs, so no barrier
+// follows it then.  Where two neighbouring
 // groups deposit the thread index's warp bits into the same position bits,
 // each warp owns the same positions on both sides of their boundary: that
 // exchange only needs __syncwarp (with the no-event partition of N = 1024,
@@ -170,19 +183,6 @@ __host__ __device__ constexpr PartitionSize partition_size(int n, int KB, int le
     return r;
 }
 
-// The largest partition over every event shape (m = level + range - 1 <= n).
-__host__ __device__ constexpr PartitionSize max_partition(int n, int KB)
-{
-    PartitionSize best = partition_size(n, KB, 0, 0);
-    for (int level = 1; level < n; ++level)
-        for (int range = 2; range <= 16 && level + range - 1 <= n; ++range) {
-            const PartitionSize p = partition_size(n, KB, level, range);
-            best.cols = p.cols > best.cols ? p.cols : best.cols;
-            best.groups = p.groups > best.groups ? p.groups : best.groups;
-        }
-    return best;
-}
-
 // Whether plane n-1 can hold L at level 2 between two single stages: single stages exist only for
 // events narrower than a group (m = level + range - 1 < KB, so at level 1 after 0 or more stages),
 // and plane n-1 is free in those partitions when their last group has at least two stages (it is
@@ -230,7 +230,6 @@ struct G3 {
     static constexpr int T = N / E;                              // threads per slot, every one owns positions
     static constexpr int NW = words_of<LOGN>();
     static constexpr int NPL = LOGN - 1;
-    static constexpr PartitionSize MAXP = max_partition(LOGN, KB);
     static constexpr bool LASTREG = tmem_last_in_regs(LOGN);     // the last group's offsets in registers
     // TMEM columns per thread: a partition's interior messages, then E shared-memory offsets per
     // register group (the last group's not when LASTREG)
