@@ -333,6 +333,7 @@ void fill_params(const pc_code* code, const float* d_llr, const pc_sched* sched,
     P->job.max_iters = max_iters;
     P->job.K = code->K;
     P->job.r = code->crc_len;
+    P->job.neg_zero = -0.0f;
 }
 
 // d_post (posterior output, nullable): the TMEM kernel's debug build that also writes L at node

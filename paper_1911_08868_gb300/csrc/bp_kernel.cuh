@@ -134,12 +134,17 @@ __device__ __forceinline__ float fnode(float a, float b, float alpha);
 // min(|a|,|b|) carrying the sign bit sign(a) XOR sign(b), one instruction
 // (min.xorsign.abs); alpha * that value has exactly the bits of alpha *
 // min(|a|,|b|) with the product sign applied afterwards, for any alpha.
-template <>
-__device__ __forceinline__ float fnode<0>(float a, float b, float alpha)
+__device__ __forceinline__ float signed_min(float a, float b)
 {
     float m;
     asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
-    return __fmul_rn(alpha, m);
+    return m;
+}
+
+template <>
+__device__ __forceinline__ float fnode<0>(float a, float b, float alpha)
+{
+    return __fmul_rn(alpha, signed_min(a, b));
 }
 
 // Hardware base-2 exponential and reciprocal (approximate, subnormals flushed).

@@ -490,10 +490,44 @@ __device__ __forceinline__ void group_offsets(const Ctl3<LOGN, KB>* c, const uns
     }
 }
 
-// One PE layer inside a thread: register e pairs with e | 2^i.
-template <int E, int FK>
-__device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float alpha)
+// alpha * m in both lanes, each lane rounded once as by __fmul_rn: a packed
+// fused multiply-add whose addend nz is -0, a value the compiler cannot see
+// (the exact product plus -0 is the exact product, and +0 + -0 = +0).  A
+// packed multiply whose result feeds a packed add is fused into one packed
+// multiply-add by ptxas (one rounding instead of two, even for mul.rn.f32x2
+// and add.rn.f32x2); a product that already is a multiply-add is left alone.
+__device__ __forceinline__ float2 scale2(float2 alpha2, float2 m, float2 nz2)
 {
+    return __ffma2_rn(alpha2, m, nz2);
+}
+
+// One PE layer inside a thread: register e pairs with e | 2^i.  For scaled
+// min-sum and a layer i > 0, the elements with tops e and e+1 (e even) run
+// together: their sums, scalings and final adds as packed two-lane FP32
+// operations, each lane rounded exactly as the scalar __fadd_rn / __fmul_rn
+// of fnode<0>, their signed minima one by one.  Layer 0 pairs e with e+1 and
+// stays scalar.
+template <int E, int FK>
+__device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float alpha, float nz)
+{
+    if (FK == 0 && i > 0) {
+        const float2 a2 = make_float2(alpha, alpha), nz2 = make_float2(nz, nz);
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+            if (e & (1 << i)) continue;
+            const int eb = e | (1 << i);
+            const float2 lt = make_float2(x[e], x[e + 1]), lb = make_float2(x[eb], x[eb + 1]);
+            const float2 s = __fadd2_rn(lb, make_float2(rv[eb], rv[eb + 1]));
+            const float2 top = scale2(a2, make_float2(signed_min(lt.x, s.x), signed_min(lt.y, s.y)), nz2);
+            const float2 g = scale2(a2, make_float2(signed_min(rv[e], lt.x), signed_min(rv[e + 1], lt.y)), nz2);
+            const float2 bot = __fadd2_rn(g, lb);
+            x[e] = top.x;
+            x[e + 1] = top.y;
+            x[eb] = bot.x;
+            x[eb + 1] = bot.y;
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         if (e & (1 << i)) continue;
@@ -505,8 +539,26 @@ __device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float 
 }
 
 template <int E, int FK>
-__device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float alpha)
+__device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float alpha, float nz)
 {
+    if (FK == 0 && i > 0) {
+        const float2 a2 = make_float2(alpha, alpha), nz2 = make_float2(nz, nz);
+#pragma unroll
+        for (int e = 0; e < E; e += 2) {
+            if (e & (1 << i)) continue;
+            const int eb = e | (1 << i);
+            const float2 rt = make_float2(y[e], y[e + 1]), rb = make_float2(y[eb], y[eb + 1]);
+            const float2 s = __fadd2_rn(make_float2(lv[eb], lv[eb + 1]), rb);
+            const float2 top = scale2(a2, make_float2(signed_min(rt.x, s.x), signed_min(rt.y, s.y)), nz2);
+            const float2 g = scale2(a2, make_float2(signed_min(rt.x, lv[e]), signed_min(rt.y, lv[e + 1])), nz2);
+            const float2 bot = __fadd2_rn(g, rb);
+            y[e] = top.x;
+            y[e + 1] = top.y;
+            y[eb] = bot.x;
+            y[eb + 1] = bot.y;
+        }
+        return;
+    }
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         if (e & (1 << i)) continue;
@@ -891,6 +943,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 
     const DevSched& S = J.S;
     const float alpha = S.alpha;
+    const float nzero = J.neg_zero;    // -0, read at run time (scale2)
     const int KW = (K + 31) / 32;
     const int max_iters = J.max_iters;
     constexpr bool want_g = WG != 0;     // the G-matrix test is on (stop_kind & 2), fixed per launch
@@ -1140,7 +1193,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         }
 #pragma unroll
                         for (int i = 0; i < GL; ++i) {
-                            l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha);
+                            l_layer<E, FK>(x, i < GL - 1 ? rp[i < GL - 1 ? i : 0] : rb, i, alpha, nzero);
                             if (i < GL - 1) tm_st<E>(tc(colL + uint32_t(i * E)), x);   // L level s0+2+i
                         }
 #pragma unroll
@@ -1214,7 +1267,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 for (int i = 0; i < GLL; ++i) {
 #pragma unroll
                     for (int e = 0; e < E; ++e) xL[i][e] = x[e];
-                    l_layer<E, FK>(x, i < GLL - 1 ? rp[i < GLL - 1 ? i : 0] : pr, i, alpha);
+                    l_layer<E, FK>(x, i < GLL - 1 ? rp[i < GLL - 1 ? i : 0] : pr, i, alpha, nzero);
                 }
                 if constexpr (PO != 0) {
                     // L at node level n+1, overwritten every iteration (the barriers between
@@ -1244,7 +1297,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 for (int e = 0; e < E; ++e) y[e] = pr[e];
 #pragma unroll
                 for (int i = GLL - 1; i >= 0; --i) {
-                    r_layer<E, FK>(y, xL[i], i, alpha);
+                    r_layer<E, FK>(y, xL[i], i, alpha, nzero);
                     if (i > 0) {
                         tm_st<E>(tc(colLL + uint32_t((GLL + i - 2) * E)), y);   // R level s0L+1+i
                     } else {
@@ -1362,7 +1415,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #pragma unroll
                         for (int i = GL - 1; i >= 0; --i) {
                             if (FIRST && i == 0 && !gtest && !PO) continue;       // stage 0 writes only the G-matrix bits
-                            r_layer<E, FK>(y, lv[i], i, alpha);
+                            r_layer<E, FK>(y, lv[i], i, alpha, nzero);
                             if (i > 0) {
                                 tm_st<E>(tc(colL + uint32_t((GL + i - 2) * E)), y);            // R level s0+1+i
                             } else if (!FIRST) {

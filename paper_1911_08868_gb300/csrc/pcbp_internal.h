@@ -51,6 +51,7 @@ struct FrameJob {
     int32_t K, r;
     unsigned* check;   // builds with PCBP_CHECKED: bit c set when an access of class c was out of range (nullable)
     float* post;       // posterior-output kernels only: [B][2][N], L at node level n+1, R at node level 1
+    float neg_zero;    // -0.0f: the addend of the packed scalings, unknown to the compiler
 };
 
 struct DevEvent {
