@@ -62,10 +62,12 @@ def _jobs() -> list[tuple[Path, Path, list[str]]]:
         extra = [f"-DPCBP_KB={int(kb)}"] if kb else []
         jobs.append((obj, CSRC / "bp_inst2.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst2.cu"), "-o", str(obj)]))
-    kb3 = os.environ.get("PCBP_KB3")    # the same override for the tensor-memory kernel
-    for n in LOGNS_TMEM:
-        obj = BUILD / (f"bp_inst3_{n}_kb{int(kb3)}.o" if kb3 else f"bp_inst3_{n}.o")
-        extra = [f"-DPCBP_KB3={int(kb3)}"] if kb3 else []
+    kb3 = os.environ.get("PCBP_KB3")    # the same override for the tensor-memory kernel, for the
+    kb3_logn = os.environ.get("PCBP_KB3_LOGN")   # lengths where a warp still owns 32 x 2^KB positions
+    for n in LOGNS_TMEM:                         # (and only log2 N in PCBP_KB3_LOGN, when given)
+        use = kb3 is not None and n - int(kb3) >= 5 and (not kb3_logn or str(n) in kb3_logn.split(","))
+        obj = BUILD / (f"bp_inst3_{n}_kb{int(kb3)}.o" if use else f"bp_inst3_{n}.o")
+        extra = [f"-DPCBP_KB3={int(kb3)}"] if use else []
         jobs.append((obj, CSRC / "bp_inst3.cu", [*common, f"-DPCBP_LOGN={n}", *extra, "-c",
                                                  str(CSRC / "bp_inst3.cu"), "-o", str(obj)]))
     for name in ("bp_decode.cu", "bp_decode_static.cu", "bp_selfcheck.cu", "wbp.cu"):
