@@ -56,17 +56,24 @@ int occupancy(const LaunchGeom& g)
         return 0;
     return blocks;
 }
+
+// Frame slots a CTA can hold by threads, TMEM columns and named barriers.
+constexpr int max_slots()
+{
+    int slots = tmem_max_threads<PCBP_LOGN, KB>() / Geo::T;
+    const int by_tmem = Geo::MAX_WARPS_TMEM / (Geo::T / 32);
+    slots = slots < by_tmem ? slots : by_tmem;
+    if (Geo::T > 32 && slots > 15) slots = 15;   // named barriers 1..15
+    return slots;
+}
+
 }  // namespace
 
 void PCBP_CAT(bp3_shape_, PCBP_LOGN)(int* threads_per_slot_out, size_t* slot_bytes_out, int* max_slots_out)
 {
     *threads_per_slot_out = Geo::T;
     *slot_bytes_out = tmem_slot_bytes<PCBP_LOGN, KB>();
-    int slots = tmem_max_threads<PCBP_LOGN, KB>() / Geo::T;
-    const int by_tmem = Geo::MAX_WARPS_TMEM / (Geo::T / 32);
-    slots = slots < by_tmem ? slots : by_tmem;
-    if (Geo::T > 32 && slots > 15) slots = 15;   // named barriers 1..15
-    *max_slots_out = slots;
+    *max_slots_out = max_slots();
 }
 
 void PCBP_CAT(bp3_tables_, PCBP_LOGN)(int N, int K, size_t* bytes) { *bytes = tmem_cta_bytes<PCBP_LOGN, KB>(N, K); }

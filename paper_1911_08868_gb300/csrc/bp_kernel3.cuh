@@ -259,7 +259,7 @@ constexpr int kTmemCols = 512;
 // contribution c_j of every position (bit i = bit i of x^(K-1-k) mod g for
 // the information bit of rank k at j, 0 for frozen positions), information
 // positions, swizzle table; the frame slots follow.
-__host__ __device__ inline size_t tmem_table_bytes(int N, int K)
+__host__ __device__ constexpr size_t tmem_table_bytes(int N, int K)
 {
     const int nw = N >= 32 ? N / 32 : 1;
     return align16(size_t(nw) * 4 + size_t(N) * 4 + size_t(K) * 2) + kSwzTableBytes;
@@ -313,7 +313,7 @@ struct Ctl3 {
     uint2 cmask[LOGN];
     alignas(16) short swoff[LOGN][2][1 << KB];
     unsigned crc_part[3];    // CRC residue of iteration it, accumulated in crc_part[it % 3]
-    unsigned pad_;
+    unsigned crc_final;      // the CRC test of the frame's final decisions: 2 passed, 1 failed, 0 not run
 };
 
 // Bytes of one frame slot: control block, decision words, NPLANES planes.
@@ -821,7 +821,7 @@ __device__ __noinline__ void single_stage(bool r_sweep, int s, int tid, int lowm
 // block of the no-event partition (built once per CTA, copied into a slot
 // whose previous frame switched partitions).
 template <int LOGN, int KB>
-__host__ __device__ inline size_t tmem_cta_bytes(int N, int K)
+__host__ __device__ constexpr size_t tmem_cta_bytes(int N, int K)
 {
     return tmem_table_bytes(N, K) + align16(sizeof(Ctl3<LOGN, KB>));
 }
@@ -1076,15 +1076,27 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         }
     };
 
-    // The slot leader fetches the next frame index as soon as the current
-    // frame's last iteration is known, so the atomic's latency overlaps the
-    // frame's output phase.
+    // Frame indices come from the launch's atomic counter.  The slot leader takes the next index
+    // as soon as the current frame's last iteration is known, so the atomic's latency overlaps
+    // the frame's output phase, and publishes it in s_next[slot] (outside the control block,
+    // which a frame start may overwrite with the no-event template while other warps of the slot
+    // have yet to read the index).
+    __shared__ long long s_next[32];
+    static_assert(tmem_max_threads<LOGN, KB>() / T <= 32, "one next-frame index per slot");
+    long long* const next_frame = &s_next[slot];
     unsigned long long next_f = 0;
     bool have_next = false;
     auto fetch_next = [&]() {
         if (tid == 0 && !have_next) {
             next_f = atomicAdd(counter, 1ull);
             have_next = true;
+        }
+    };
+    // the slot leader's fetched index to s_next (visible after the next slot barrier)
+    auto publish_next = [&]() {
+        if (tid == 0) {
+            *next_frame = (long long)next_f;
+            have_next = false;
         }
     };
     bool fresh = false;     // the control block holds the no-event partition and the TMEM caches match it
@@ -1094,19 +1106,16 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         Rp[Geo::PRIOR * N + sw(j)] = prior_of(s_frozen, j);
         Rp[Geo::CJ * N + sw(j)] = __int_as_float(int(s_cj[j]));
     }
+    fetch_next();
+    publish_next();
+    sync();
     while (true) {
-        fetch_next();
-        if (tid == 0) {
-            ctl->g.frame = (long long)next_f;
-            have_next = false;
-        }
-        sync();
-        const long long f = ctl->g.frame;
+        const long long f = *next_frame;     // published before a slot barrier
         if (f >= J.B) break;
         const float* llr_f = J.llr + size_t(f) * N;
-        // a1: the frame's channel LLRs stream into plane n-1 (free between frames) as 16-byte
-        // asynchronous copies, while the planes are cleared; the first group's threads then read
-        // their positions from shared memory
+        // a1: the frame's channel LLRs stream into the spare plane (free between frames) as
+        // 16-byte asynchronous copies, while the planes are cleared; the first group's threads
+        // then read their positions from shared memory
         float* s_llr = Rp + Geo::SPARE * N;
         {
             const uint32_t d = uint32_t(__cvta_generic_to_shared(s_llr));
@@ -1117,7 +1126,22 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                              : "memory");
         }
 
-        for (int i = tid; i < NPL * N / 4; i += T) reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (fresh) {
+            // the no-event partition (groups of KB stages from stage 0, the short one last) reads
+            // R at its group boundaries, levels KB+1, 2KB+1, ... (planes KB-1, 2KB-1, ...) before
+            // writing them; its interior R levels restart in TMEM, and the planes of those levels
+            // hold group inputs, written before they are read
+            constexpr int NBP = (LOGN - 1) / KB;
+            for (int i = tid; i < NBP * N / 4; i += T) {
+                const int k = i / (N / 4);
+                reinterpret_cast<float4*>(Rp + ((k + 1) * KB - 1) * N)[i - k * (N / 4)] =
+                    make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            // enter_partition reads the no-event partition's interior R from the planes
+            for (int i = tid; i < NPL * N / 4; i += T)
+                reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         for (int i = tid; i < NW; i += T) {
             dec[i] = 0u;
             xh[i] = 0u;
@@ -1140,6 +1164,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
         // L sweep overwrites with boundary L messages: every thread's reads come first
         if (fresh) restart_partition(s_llr);
         else enter_partition(s_llr);
+        if (tid == 0) ctl->crc_final = 0u;
         sync();
         fresh = true;
 
@@ -1350,6 +1375,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             if (!want_g) {
                 const bool stop = check && res == 0u;
                 if (stop || it == max_iters) {
+                    if (tid == 0 && check) ctl->crc_final = stop ? 2u : 1u;    // read after the barrier below
                     fetch_next();
                     // the decision words, once per frame: where every thread's register bits are
                     // position bits 0..KB-1 (class 0, in stage order), 32/E neighbouring lanes
@@ -1531,7 +1557,7 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                         const int m = lv + rg - 1;
                         const int span = 1 << m;
                         for (int i = tid; i < (rg - 1) * span; i += T) {
-                            const int lev = lv + 1 + i / span;       // node level, 2..n
+                            const int lev = lv + 1 + (i >> m);       // node level, 2..n
                             int j = int(bk) + ((i & (span - 1)) << (n - m));
                             int plane = lev - 2;
 #ifdef PCBP_CHECKED
@@ -1555,15 +1581,22 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 
         // a7: outputs
         fetch_next();
+        publish_next();
         {
-            uint32_t part = 0;
+            // the CRC flag: from the residue of the final decisions where the last iteration
+            // computed it, else from the decision words
+            const unsigned crc_final = ctl->crc_final;
+            const bool crc_known = crc_final != 0u;
+            if (!crc_known) {
+                uint32_t part = 0;
 #pragma unroll
-            for (int j = tid; j < N; j += T)
-                if ((dec[j >> 5] >> (j & 31)) & 1u) part ^= s_cj[j];
-            part = __reduce_xor_sync(0xffffffffu, part);
-            if (tid == 0) ctl->g.crc_res = 0;
-            sync();
-            if (lane == 0 && part) atomicXor(reinterpret_cast<unsigned*>(&ctl->g.crc_res), part);
+                for (int j = tid; j < N; j += T)
+                    if ((dec[j >> 5] >> (j & 31)) & 1u) part ^= s_cj[j];
+                part = __reduce_xor_sync(0xffffffffu, part);
+                if (tid == 0) ctl->g.crc_res = 0;
+                sync();
+                if (lane == 0 && part) atomicXor(reinterpret_cast<unsigned*>(&ctl->g.crc_res), part);
+            }
             for (int o = warp; o < KW; o += NWARP) {
                 const int kk = o * 32 + lane;
                 uint32_t bit = 0;
@@ -1576,10 +1609,10 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
             }
             sync();
             if (tid == 0) {
-                J.crc_ok[f] = ctl->g.crc_res == 0 ? 1 : 0;
+                J.crc_ok[f] = crc_known ? uint8_t(crc_final - 1u) : (ctl->g.crc_res == 0 ? 1 : 0);
                 J.iters[f] = used;
             }
-            sync();
+            if (!crc_known) sync();     // crc_res is read before a frame start may overwrite the control block
         }
     }
     tm_wait_st();
