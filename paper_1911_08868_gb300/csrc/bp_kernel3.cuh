@@ -693,11 +693,25 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
     if (lane == 0) c->g.ng = ng;
 }
 
+// x mod d for 0 < d < 2^16, equal to the 64-bit remainder: with x = hi 2^32 + lo,
+// x = (hi mod d)(2^32 mod d) + (lo mod d) (mod d), and that sum is at most (d - 1)^2 + d - 1 <
+// 2^32, so 32-bit remainders give it (a 64-bit remainder by a run-time divisor is a long
+// serial subroutine).
+__device__ __forceinline__ uint32_t mod_small(uint64_t x, uint32_t d)
+{
+    const uint32_t hi = uint32_t(x >> 32), lo = uint32_t(x);
+    const uint32_t p = (0u - d) % d;      // 2^32 mod d
+    return ((hi % d) * p + lo % d) % d;
+}
+
 // draw_event (bp_kernel.cuh) computed by the 32 lanes of a warp: lane d
-// evaluates draw d of the event's counter-based stream, every lane then makes
-// the same choices from those values (fetched with shuffles; draws past 31,
-// needed only after a second identity permutation, are evaluated directly).
-// Same draws and same choices, so the same event.
+// evaluates draw d of the event's counter-based stream and reduces it by the
+// divisor that draw meets (lanes 0 and 1: range and level; lanes 3 + 16 a + t:
+// the Fisher-Yates draw t of attempt a, modulo range - t), every lane then
+// makes the same choices from those values (fetched with shuffles; draws past
+// 31, needed only from the third attempt on or for ranges above 13, are
+// evaluated directly).  The block draw is reduced modulo a power of two, a
+// mask.  Same draws, same remainders and same choices, so the same event.
 __device__ __forceinline__ void draw_event_warp(const DevSched& S, int n, uint64_t frame, int k, int lane, int& level,
                                                 int& range, long long& block, signed char* order)
 {
@@ -715,16 +729,26 @@ __device__ __forceinline__ void draw_event_warp(const DevSched& S, int n, uint64
         level = 1;
         block = 0;
     } else {
-        range = S.rho_fixed > 0 ? S.rho_fixed : 2 + int(draw(0) % uint64_t(S.P_range - 1));
-        const int x = 1 + int(draw(1) % uint64_t(S.P_level));
+        const uint32_t dv = lane == 0 ? uint32_t(S.P_range > 2 ? S.P_range - 1 : 1) : uint32_t(S.P_level > 1 ? S.P_level : 1);
+        const uint32_t red = mod_small(mine, dv);
+        const uint32_t r0 = __shfl_sync(0xffffffffu, red, 0), r1 = __shfl_sync(0xffffffffu, red, 1);
+        range = S.rho_fixed > 0 ? S.rho_fixed : 2 + int(r0);
+        const int x = 1 + int(r1);
         level = min(x, n - range + 1);
         const int m = level + range - 1;
-        block = (long long)(draw(2) % (1ull << (n - m)));
+        block = (long long)(draw(2) & ((1ull << (n - m)) - 1ull));
+    }
+    uint32_t jr = 0;     // this lane's Fisher-Yates remainder (lanes 3 .. 31)
+    {
+        const int t = (lane - 3) & 15;
+        if (lane >= 3 && t < range - 1) jr = mod_small(mine, uint32_t(range - t));
     }
     for (int attempt = 0; attempt < 8; ++attempt) {
         for (int i = 0; i < range; ++i) order[i] = (signed char)i;
         for (int i = range - 1; i >= 1; --i) {
-            const int j = int(draw(3 + 16 * attempt + (range - 1 - i)) % uint64_t(i + 1));
+            const int dl = 3 + 16 * attempt + (range - 1 - i);
+            const int j = dl < 32 ? int(__shfl_sync(0xffffffffu, jr, dl))
+                                  : int(mod_small(event_draw(S.seed, frame, uint64_t(k), uint64_t(dl)), uint32_t(i + 1)));
             const signed char t = order[i];
             order[i] = order[j];
             order[j] = t;
@@ -1549,7 +1573,14 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     sync();
                     // the message reset of Sec. III: R at the interior levels of the previous
                     // subgraph (reverting to the original order) and of the new one
-                    for (int pass = 0; pass < 2; ++pass) {
+                    // (an event over the whole graph, as in FP-BP, resets every R plane: 16-byte
+                    // stores, and the previous subgraph needs no pass of its own)
+                    const bool whole = ctl->g.ev_level == 1 && ctl->g.ev_range == n;
+                    if (whole) {
+                        for (int i = tid; i < NPL * N / 4; i += T)
+                            reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                    for (int pass = 0; pass < 2 && !whole; ++pass) {
                         if (pass == 0 && !ctl->g.have_prev) continue;
                         const int lv = pass == 0 ? ctl->g.pv_level : ctl->g.ev_level;
                         const int rg = pass == 0 ? ctl->g.pv_range : ctl->g.ev_range;
