@@ -569,19 +569,25 @@ __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float 
     }
 }
 
+// Entry i of a stage order packed as 4-bit fields (range <= 16).
+__device__ __forceinline__ int order_at(uint64_t ord, int i) { return int((ord >> (4 * i)) & 15u); }
+
 // The partition of build_groups (short_last) plus pack_groups, computed by
 // the 32 lanes of one warp: every lane walks the group list (a few dozen
 // steps), lane 2g + c then builds group g's register bits for class c, and
 // the lane pairs exchange what the packed record needs.  Writes g.ng, g.low,
 // g.beta, g.pbit and the packed records (rec, cmask, swoff) that the TMEM
-// kernel reads; the per-class bit lists of GroupCtl are not kept.
+// kernel reads; the per-class bit lists of GroupCtl are not kept.  The event's
+// stage order comes packed (order_at); segments, register bits and order live
+// in registers (no local-memory arrays).
 template <int LOGN, int KB>
-__device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsigned char* swt, int level, int range,
-                                                  long long blk, const signed char* order, int lane)
+__device__ __forceinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsigned char* swt, int level, int range,
+                                                     long long blk, uint64_t ord, int lane)
 {
     constexpr int n = LOGN;
     constexpr int E = 1 << KB;
     constexpr int TB = LOGN - KB;
+    static_assert(5 * KB <= 32, "register bits packed 5 bits each");
     const int lo = level - 1, hi = level + range - 2, m = hi + 1;
     if (lane == 0) {
         c->g.low = n - m;
@@ -589,70 +595,80 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
     }
     if (lane < 16) {
         int pb = n - 1 - lane;
-        if (lane >= lo && lane <= hi) pb = n - level - order[lane - lo];
+        if (lane >= lo && lane <= hi) pb = n - level - order_at(ord, lane - lo);
         c->g.pbit[lane] = (signed char)pb;
     }
-    // segments [a, b, kind]: 0 homogeneous, 1 subgraph-local, 2 single stages
-    int seg_a[3], seg_b[3], seg_k[3], nseg = 0;
-    if (m >= KB) {
-        seg_a[nseg] = 0; seg_b[nseg] = hi; seg_k[nseg] = 1; ++nseg;
-        if (hi + 1 <= n - 1) { seg_a[nseg] = hi + 1; seg_b[nseg] = n - 1; seg_k[nseg] = 0; ++nseg; }
-    } else {
-        if (lo >= 1) { seg_a[nseg] = 0; seg_b[nseg] = lo - 1; seg_k[nseg] = 0; ++nseg; }
-        seg_a[nseg] = lo; seg_b[nseg] = hi; seg_k[nseg] = 2; ++nseg;
-        if (hi + 1 <= n - 1) { seg_a[nseg] = hi + 1; seg_b[nseg] = n - 1; seg_k[nseg] = 0; ++nseg; }
-    }
+    // segments [a, b, kind]: 0 homogeneous, 1 subgraph-local, 2 single stages; segment sg of
+    // at most 3, computed where it is used
+    const bool wide = m >= KB;
+    const bool head = !wide && lo >= 1;          // homogeneous stages before the single ones
+    const bool tail = hi + 1 <= n - 1;           // homogeneous stages after the event
+    const int nseg = (wide ? 1 : (head ? 2 : 1)) + (tail ? 1 : 0);
+    auto seg = [&](int sg, int& a, int& b, int& kind) {
+        if (wide) {
+            if (sg == 0) { a = 0; b = hi; kind = 1; }
+            else { a = hi + 1; b = n - 1; kind = 0; }
+        } else {
+            const int q = head ? sg : sg + 1;      // 0 head, 1 single stages, 2 tail
+            if (q == 0) { a = 0; b = lo - 1; kind = 0; }
+            else if (q == 1) { a = lo; b = hi; kind = 2; }
+            else { a = hi + 1; b = n - 1; kind = 0; }
+        }
+    };
     // walk the groups: this lane's group gi = lane / 2, its columns before it
     const int gi = lane >> 1, cls = lane & 1;
     int ng = 0, my_s0 = 0, my_gl = 0, my_kind = -1, col = 0, acol = 0;
-    int my_col = 0, my_acol = 0, last_s0 = 0, last_gl = 0, last_kind = 0, last_col = 0;
-    for (int sg = 0; sg < nseg; ++sg) {
-        const int a = seg_a[sg], b = seg_b[sg], kind = seg_k[sg];
-        const int len = b - a + 1;
-        const int first = len % KB == 0 ? KB : len % KB;
-        const bool sl = sg == nseg - 1;
-        int st = a;
-        for (int q = 0; st <= b; ++q) {
-            const int gl = kind == 2 ? 1 : (sl ? (b - st + 1 < KB ? b - st + 1 : KB) : (q == 0 ? first : KB));
-            if (ng == gi) {
-                my_s0 = st; my_gl = gl; my_kind = kind; my_col = col; my_acol = acol;
+    int my_col = 0, my_acol = 0, last_gl = 0, last_col = 0;
+#pragma unroll
+    for (int sg = 0; sg < 3; ++sg) {
+        if (sg < nseg) {
+            int a = 0, b = 0, kind = 0;
+            seg(sg, a, b, kind);
+            const int len = b - a + 1;
+            const int first = len % KB == 0 ? KB : len % KB;
+            const bool sl = sg == nseg - 1;
+            int st = a;
+            for (int q = 0; st <= b; ++q) {
+                const int gl = kind == 2 ? 1 : (sl ? (b - st + 1 < KB ? b - st + 1 : KB) : (q == 0 ? first : KB));
+                if (ng == gi) {
+                    my_s0 = st; my_gl = gl; my_kind = kind; my_col = col; my_acol = acol;
+                }
+                last_gl = gl; last_col = col;
+                if (kind != 2) {
+                    col += 2 * (gl - 1) * E;   // the last group's columns are counted from its R levels below
+                    acol += E;
+                }
+                ++ng;
+                st += gl;
             }
-            last_s0 = st; last_gl = gl; last_kind = kind; last_col = col;
-            if (kind != 2) {
-                col += 2 * (gl - 1) * E;   // the last group's columns are counted from its R levels below
-                acol += E;
-            }
-            ++ng;
-            st += gl;
         }
     }
-    (void)last_s0; (void)last_kind;
     const bool mine = gi < ng;
     const bool single = my_kind == 2;
     const bool last = gi == ng - 1;
     // the offsets follow this partition's interior columns (the last group stores R levels only)
     const int interior = last_col + (last_gl - 1) * E;
     const bool cached = mine && !single && !(last && G3<LOGN, KB>::LASTREG);
-    // register bits of (gi, cls)
+    // register bits of (gi, cls): position bit of register bit i in bits 5i..5i+4 of P
     unsigned used = 0, cmask = 0;
     int contig = -1;
     if (mine && !single) {
-        signed char P[KB];
+        unsigned P = 0;
         for (int i = 0; i < my_gl; ++i) {
             const int stg = my_s0 + i;
             int bit = n - 1 - stg;
-            if (cls == 1 && my_kind == 1 && stg >= lo && stg <= hi) bit = n - level - order[stg - lo];
-            P[i] = (signed char)bit;
+            if (cls == 1 && my_kind == 1 && stg >= lo && stg <= hi) bit = n - level - order_at(ord, stg - lo);
+            P |= unsigned(bit) << (5 * i);
             used |= 1u << bit;
         }
         const int floor_bit = my_kind == 1 ? n - m : 0;
         int nxt = my_gl;
         for (int bit = n - 1 - (my_s0 + my_gl); bit >= floor_bit && nxt < KB; --bit)
-            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+            if (!((used >> bit) & 1u)) { P |= unsigned(bit) << (5 * nxt++); used |= 1u << bit; }
         for (int bit = n - my_s0; bit <= n - 1 && nxt < KB; ++bit)
-            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+            if (!((used >> bit) & 1u)) { P |= unsigned(bit) << (5 * nxt++); used |= 1u << bit; }
         for (int bit = floor_bit; bit <= n - 1 && nxt < KB; ++bit)
-            if (!((used >> bit) & 1u)) { P[nxt++] = (signed char)bit; used |= 1u << bit; }
+            if (!((used >> bit) & 1u)) { P |= unsigned(bit) << (5 * nxt++); used |= 1u << bit; }
         cmask = ((1u << n) - 1u) & ~used;
         const int lowb = __ffs(used) - 1;
         contig = (used >> lowb) == ((1u << KB) - 1u) ? lowb : -1;
@@ -661,7 +677,7 @@ __device__ __noinline__ void build_partition_warp(Ctl3<LOGN, KB>* c, const unsig
             int off = 0;
 #pragma unroll
             for (int i = 0; i < KB; ++i)
-                if ((e >> i) & 1) off |= 1 << P[i];
+                if ((e >> i) & 1) off |= 1 << ((P >> (5 * i)) & 31u);
             c->swoff[gi][cls][e] = (short)swz(swt, off);
         }
     }
@@ -713,7 +729,7 @@ __device__ __forceinline__ uint32_t mod_small(uint64_t x, uint32_t d)
 // evaluated directly).  The block draw is reduced modulo a power of two, a
 // mask.  Same draws, same remainders and same choices, so the same event.
 __device__ __forceinline__ void draw_event_warp(const DevSched& S, int n, uint64_t frame, int k, int lane, int& level,
-                                                int& range, long long& block, signed char* order)
+                                                int& range, long long& block, uint64_t& ord)
 {
     const uint64_t mine = event_draw(S.seed, frame, uint64_t(k), uint64_t(lane));
     auto draw = [&](int d) -> uint64_t {
@@ -743,29 +759,34 @@ __device__ __forceinline__ void draw_event_warp(const DevSched& S, int n, uint64
         const int t = (lane - 3) & 15;
         if (lane >= 3 && t < range - 1) jr = mod_small(mine, uint32_t(range - t));
     }
+    // the order packed 4 bits per entry (order_at); Fisher-Yates swaps exchange two fields
+    uint64_t ident = 0, rot = 0;
+    for (int i = 0; i < range; ++i) {
+        ident |= uint64_t(i) << (4 * i);
+        rot |= uint64_t((i + 1) % range) << (4 * i);
+    }
     for (int attempt = 0; attempt < 8; ++attempt) {
-        for (int i = 0; i < range; ++i) order[i] = (signed char)i;
+        uint64_t v = ident;
         for (int i = range - 1; i >= 1; --i) {
             const int dl = 3 + 16 * attempt + (range - 1 - i);
             const int j = dl < 32 ? int(__shfl_sync(0xffffffffu, jr, dl))
                                   : int(mod_small(event_draw(S.seed, frame, uint64_t(k), uint64_t(dl)), uint32_t(i + 1)));
-            const signed char t = order[i];
-            order[i] = order[j];
-            order[j] = t;
+            const uint64_t x = ((v >> (4 * i)) ^ (v >> (4 * j))) & 15u;
+            v ^= (x << (4 * i)) | (x << (4 * j));
         }
-        bool ident = true;
-        for (int i = 0; i < range; ++i) ident = ident && (order[i] == i);
-        if (!ident) return;
+        if (v != ident) {
+            ord = v;
+            return;
+        }
     }
-    for (int i = 0; i < range; ++i) order[i] = (signed char)((i + 1) % range);
+    ord = rot;
 }
 
 // Records event (level, range, blk) of frame `frame` (Sec. III) as the current
 // event (the previous one becomes the event to revert) and sets the increment
-// of N_it,reset (Eq. 2).  Slot leader only; out of line, so that the
-// iteration loop stays compact.
+// of N_it,reset (Eq. 2).  One thread.
 template <int LOGN, int KB>
-__device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S, int level, int range, long long blk)
+__device__ __forceinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S, int level, int range, long long blk)
 {
     ctl->g.pv_level = ctl->g.ev_level;
     ctl->g.pv_range = ctl->g.ev_range;
@@ -784,6 +805,22 @@ __device__ __noinline__ void apply_event(Ctl3<LOGN, KB>* ctl, const DevSched& S,
         inc = qz > S.N_min ? qz : S.N_min;
     }
     ctl->g.next_inc = int(inc);
+}
+
+// A switch's event and partition (Sec. III), by the first warp of a slot: the event draws
+// (draw_event_warp), their record (apply_event, lane 0) and the new partition
+// (build_partition_warp).  Out of line, one call per switch, so that the iteration loop stays
+// compact.
+template <int LOGN, int KB>
+__device__ __noinline__ void switch_event_warp(Ctl3<LOGN, KB>* ctl, const DevSched& S, const unsigned char* swt,
+                                               uint64_t frame, int k, int lane)
+{
+    int level = 0, range = 0;
+    long long blk = 0;
+    uint64_t ord = 0;
+    draw_event_warp(S, LOGN, frame, k, lane, level, range, blk, ord);
+    if (lane == 0) apply_event<LOGN, KB>(ctl, S, level, range, blk);
+    build_partition_warp<LOGN, KB>(ctl, swt, level, range, blk, ord, lane);
 }
 
 // One permuted stage s narrower than a register group (m < KB events), with
@@ -1560,15 +1597,8 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     tm_wait_st();
                     leave_partition();     // interior R of the old partition to the canonical planes
                     sync();
-                    if (warp == 0) {
-                        // the first warp draws the event and builds the partition
-                        int level = 0, range = 0;
-                        long long blk = 0;
-                        signed char order[16];
-                        draw_event_warp(S, n, S.frame_base + uint64_t(f), kev, lane, level, range, blk, order);
-                        if (lane == 0) apply_event<LOGN, KB>(ctl, S, level, range, blk);
-                        build_partition_warp<LOGN, KB>(ctl, s_swz, level, range, blk, order, lane);
-                    }
+                    // the first warp draws the event and builds the partition
+                    if (warp == 0) switch_event_warp<LOGN, KB>(ctl, S, s_swz, S.frame_base + uint64_t(f), kev, lane);
                     fresh = false;
                     sync();
                     // the message reset of Sec. III: R at the interior levels of the previous

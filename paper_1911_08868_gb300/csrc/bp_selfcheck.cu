@@ -52,7 +52,9 @@ __global__ void partition_selfcheck_kernel(int32_t* result)
                     pack_groups<LOGN, KB>(&A);
                 }
                 __syncwarp();
-                build_partition_warp<LOGN, KB>(&B, tab, level, range, blk, order, lane);
+                uint64_t ord = 0;
+                for (int i = 0; i < range; ++i) ord |= uint64_t(order[i]) << (4 * i);
+                build_partition_warp<LOGN, KB>(&B, tab, level, range, blk, ord, lane);
                 __syncwarp();
                 if (lane == 0) {
                     int d = (A.g.ng != B.g.ng) + (A.g.low != B.g.low) + (A.g.beta != B.g.beta);
