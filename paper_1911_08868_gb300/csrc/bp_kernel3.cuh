@@ -1594,30 +1594,24 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                 bool allowed = true;
                 if (S.mode == 2 && S.q_max > 0) allowed = kev < S.q_max - 1;
                 if (allowed) {
-                    tm_wait_st();
-                    leave_partition();     // interior R of the old partition to the canonical planes
-                    sync();
-                    // the first warp draws the event and builds the partition
-                    if (warp == 0) switch_event_warp<LOGN, KB>(ctl, S, s_swz, S.frame_base + uint64_t(f), kev, lane);
-                    fresh = false;
-                    sync();
-                    // the message reset of Sec. III: R at the interior levels of the previous
-                    // subgraph (reverting to the original order) and of the new one
-                    // (an event over the whole graph, as in FP-BP, resets every R plane: 16-byte
-                    // stores, and the previous subgraph needs no pass of its own)
-                    const bool whole = ctl->g.ev_level == 1 && ctl->g.ev_range == n;
-                    if (whole) {
-                        for (int i = tid; i < NPL * N / 4; i += T)
-                            reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
-                    for (int pass = 0; pass < 2 && !whole; ++pass) {
-                        if (pass == 0 && !ctl->g.have_prev) continue;
-                        const int lv = pass == 0 ? ctl->g.pv_level : ctl->g.ev_level;
-                        const int rg = pass == 0 ? ctl->g.pv_range : ctl->g.ev_range;
-                        const long long bk = pass == 0 ? ctl->g.pv_blk : ctl->g.ev_blk;
+                    // the message reset of Sec. III zeroes R at the interior levels of the subgraph
+                    // being left (reverting to the original order) and of the new one.  The event
+                    // being left is read before the barrier after which the first warp records the
+                    // new one; the other warps reset its subgraph while the first draws the new event.
+                    const int pv_lv = ctl->g.ev_level, pv_rg = ctl->g.ev_range;
+                    const long long pv_bk = ctl->g.ev_blk;
+                    const bool pv_have = ctl->g.have_ev != 0;
+                    // zero R at node levels lv+1 .. lv+rg-1 of block bk, threads t0, t0 + nt, ...
+                    // (an event over the whole graph, as in FP-BP: every R plane, 16-byte stores)
+                    auto reset_block = [&](int lv, int rg, long long bk, int t0, int nt) {
+                        if (lv == 1 && rg == n) {
+                            for (int i = t0; i < NPL * N / 4; i += nt)
+                                reinterpret_cast<float4*>(Rp)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+                            return;
+                        }
                         const int m = lv + rg - 1;
                         const int span = 1 << m;
-                        for (int i = tid; i < (rg - 1) * span; i += T) {
+                        for (int i = t0; i < (rg - 1) * span; i += nt) {
                             const int lev = lv + 1 + (i >> m);       // node level, 2..n
                             int j = int(bk) + ((i & (span - 1)) << (n - m));
                             int plane = lev - 2;
@@ -1630,7 +1624,18 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
 #endif
                             Rp[plane * N + sw(j)] = 0.f;
                         }
-                    }
+                    };
+                    tm_wait_st();
+                    leave_partition();     // interior R of the old partition to the canonical planes
+                    sync();
+                    // the first warp draws the event and builds the partition
+                    if (warp == 0) switch_event_warp<LOGN, KB>(ctl, S, s_swz, S.frame_base + uint64_t(f), kev, lane);
+                    else if (pv_have) reset_block(pv_lv, pv_rg, pv_bk, tid - 32, T - 32);
+                    if (T == 32 && pv_have) reset_block(pv_lv, pv_rg, pv_bk, tid, T);    // a one-warp slot
+                    fresh = false;
+                    sync();
+                    if (!(pv_have && pv_lv == 1 && pv_rg == n && ctl->g.ev_level == 1 && ctl->g.ev_range == n))
+                        reset_block(ctl->g.ev_level, ctl->g.ev_range, ctl->g.ev_blk, tid, T);
                     next_reset = it + ctl->g.next_inc;
                     ++kev;
                     sync();
