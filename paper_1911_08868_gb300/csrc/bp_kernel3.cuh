@@ -314,6 +314,13 @@ struct Ctl3 {
     alignas(16) short swoff[LOGN][2][1 << KB];
     unsigned crc_part[3];    // CRC residue of iteration it, accumulated in crc_part[it % 3]
     unsigned crc_final;      // the CRC test of the frame's final decisions: 2 passed, 1 failed, 0 not run
+    // events drawn ahead: nx[k & 1] holds event k of frame nx[.].frame, drawn by a spare warp during
+    // switch k - 1 (k = -1: none)
+    struct Drawn {
+        int k, level, range, frame;
+        long long blk;
+        unsigned long long ord;
+    } nx[2];
 };
 
 // Bytes of one frame slot: control block, decision words, NPLANES planes.
@@ -818,9 +825,37 @@ __device__ __noinline__ void switch_event_warp(Ctl3<LOGN, KB>* ctl, const DevSch
     int level = 0, range = 0;
     long long blk = 0;
     uint64_t ord = 0;
-    draw_event_warp(S, LOGN, frame, k, lane, level, range, blk, ord);
+    const auto& d = ctl->nx[k & 1];
+    if (d.k == k && d.frame == int(frame)) {      // drawn ahead during the previous switch
+        level = d.level;
+        range = d.range;
+        blk = d.blk;
+        ord = d.ord;
+    } else {
+        draw_event_warp(S, LOGN, frame, k, lane, level, range, blk, ord);
+    }
     if (lane == 0) apply_event<LOGN, KB>(ctl, S, level, range, blk);
     build_partition_warp<LOGN, KB>(ctl, swt, level, range, blk, ord, lane);
+}
+
+// Event k of a frame drawn ahead by a warp that would otherwise wait, during switch k - 1 (the
+// draws depend on the seed, the frame and k only), into nx[k & 1], which that switch does not read.
+template <int LOGN, int KB>
+__device__ __noinline__ void predraw_event_warp(Ctl3<LOGN, KB>* ctl, const DevSched& S, uint64_t frame, int k, int lane)
+{
+    int level = 0, range = 0;
+    long long blk = 0;
+    uint64_t ord = 0;
+    draw_event_warp(S, LOGN, frame, k, lane, level, range, blk, ord);
+    if (lane == 0) {
+        auto& d = ctl->nx[k & 1];
+        d.level = level;
+        d.range = range;
+        d.blk = blk;
+        d.ord = ord;
+        d.frame = int(frame);
+        d.k = k;
+    }
 }
 
 // One permuted stage s narrower than a register group (m < KB events), with
@@ -906,6 +941,8 @@ __device__ __noinline__ void build_template(Ctl3<LOGN, KB>* c, const unsigned ch
     c->crc_part[0] = 0u;
     c->crc_part[1] = 0u;
     c->crc_part[2] = 0u;
+    c->nx[0].k = -1;
+    c->nx[1].k = -1;
     signed char none[16];
     build_groups<LOGN, KB>(&c->g, s_swz, LOGN, false, 0, 0, 0, none, true);
     pack_groups<LOGN, KB>(c);
@@ -1628,10 +1665,20 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
                     tm_wait_st();
                     leave_partition();     // interior R of the old partition to the canonical planes
                     sync();
-                    // the first warp draws the event and builds the partition
-                    if (warp == 0) switch_event_warp<LOGN, KB>(ctl, S, s_swz, S.frame_base + uint64_t(f), kev, lane);
-                    else if (pv_have) reset_block(pv_lv, pv_rg, pv_bk, tid - 32, T - 32);
-                    if (T == 32 && pv_have) reset_block(pv_lv, pv_rg, pv_bk, tid, T);    // a one-warp slot
+                    // the first warp draws the event (unless drawn ahead) and builds the partition;
+                    // in slots of four warps or more the second draws the next switch's event
+                    // ahead, and the remaining warps reset the subgraph being left (a one-warp slot
+                    // does that after the partition)
+                    const uint64_t fid = S.frame_base + uint64_t(f);
+                    constexpr int RW = T >= 128 ? 64 : 32;     // the first thread of the resetting warps
+                    if (warp == 0) {
+                        switch_event_warp<LOGN, KB>(ctl, S, s_swz, fid, kev, lane);
+                        if (T == 32 && pv_have) reset_block(pv_lv, pv_rg, pv_bk, tid, T);
+                    } else if (T >= 128 && warp == 1) {
+                        predraw_event_warp<LOGN, KB>(ctl, S, fid, kev + 1, lane);
+                    } else if (pv_have) {
+                        reset_block(pv_lv, pv_rg, pv_bk, tid - RW, T - RW);
+                    }
                     fresh = false;
                     sync();
                     if (!(pv_have && pv_lv == 1 && pv_rg == n && ctl->g.ev_level == 1 && ctl->g.ev_range == n))
