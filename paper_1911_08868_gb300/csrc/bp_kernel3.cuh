@@ -1075,27 +1075,30 @@ __device__ __forceinline__ void tmem_frames(const FrameJob& J, unsigned long lon
     // interior R messages, channel LLRs of group 0's positions (from llr_src,
     // in natural position order).
     auto restart_partition = [&](const float* llr_src) {
-        const int ng = ctl->g.ng;
+        // the no-event partition has (n + KB - 1) / KB groups and no single stages: the group
+        // loop is unrolled, so the records and the first group's offsets load at once
+        constexpr int NG0 = (LOGN + KB - 1) / KB;
+#ifdef PCBP_CHECKED
+        if (ctl->g.ng != NG0) chk_fail(J.check, 6);
+#endif
         float z[E];
 #pragma unroll
         for (int e = 0; e < E; ++e) z[e] = 0.f;
-        #pragma unroll 1
-        for (int gi = 0; gi < ng; ++gi) {
+        int A[E];
+        tm_ld_i<E>(tc(uint32_t(ctl->rec[0].w)), A);
+#pragma unroll
+        for (int gi = 0; gi < NG0; ++gi) {
             const int4 rc = ctl->rec[gi];
             const int gl = (rc.x >> 8) & 0xff;
-            if ((rc.x >> 16) & 1) continue;
             const uint32_t colR = uint32_t(rc.y + (gl - 1) * E);
-            #pragma unroll 1
-            for (int i = 0; i < gl - 1; ++i) tm_st<E>(tc(colR + uint32_t(i * E)), z);
-            if (gi == 0) {
-                int A[E];
-                tm_ld_i<E>(tc(uint32_t(rc.w)), A);
-                tm_wait_ld();
-                tm_fence<E>(A);
 #pragma unroll
-                for (int e = 0; e < E; ++e) L1[e] = llr_src[pos_of(A[e], 0)];
-            }
+            for (int i = 0; i < KB - 1; ++i)
+                if (i < gl - 1) tm_st<E>(tc(colR + uint32_t(i * E)), z);
         }
+        tm_wait_ld();
+        tm_fence<E>(A);
+#pragma unroll
+        for (int e = 0; e < E; ++e) L1[e] = llr_src[pos_of(A[e], 0)];
         tm_wait_st();
     };
 
