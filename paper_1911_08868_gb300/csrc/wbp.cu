@@ -242,9 +242,15 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
         copy_wait();
         bar(bid, tps);
         for (int it = 0; it < P.T; ++it) {
+            // the thread's weight pairs, each loaded one stage ahead of its use (read-only data,
+            // so the load may be issued before the barrier that ends the previous stage)
             const float* wq = P.w + size_t(it) * n * NH * 4 + size_t(q) * 4;
+            float2 wc = ld_pair(wq);
 #pragma unroll
             for (int s = 0; s < n; ++s) {
+                const float2 w2 = wc;                          // k = 0, 1
+                if (s + 1 < n) wc = ld_pair(wq + (s + 1) * NH * 4);
+                else if (it + 1 < P.T) wc = ld_pair(wq + (n - 1) * NH * 4 + 2);
                 if (act) {
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
@@ -252,7 +258,6 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                     const float* Rs = R + s * N;           // level s+2
                     float* Lo = L + (s + 1) * N;
                     const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
-                    const float2 w2 = ld_pair(wq + s * NH * 4);   // k = 0, 1
                     Lo[t] = fw(lt, radd(lb, rb), w2.x);
                     Lo[b] = radd(fw(rt, lt, w2.y), lb);
                 }
@@ -261,6 +266,8 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
             if (it == P.T - 1) break;
 #pragma unroll
             for (int s = n - 1; s >= 1; --s) {
+                const float2 w2 = wc;                          // k = 2, 3
+                if (s > 1) wc = ld_pair(wq + (s - 1) * NH * 4 + 2);
                 if (act) {
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
@@ -268,7 +275,6 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                     const float* Rs = R + s * N;           // level s+2
                     float* Ro = R + (s - 1) * N;           // level s+1
                     const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
-                    const float2 w2 = ld_pair(wq + s * NH * 4 + 2);   // k = 2, 3
                     Ro[t] = fw(rt, radd(lb, rb), w2.x);
                     Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
@@ -537,6 +543,11 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
 #pragma unroll
         for (int k = 0; k < 4; ++k) dwr[s][k] = 0.f;
 
+    // the thread's weight pairs of this iteration, each loaded one stage ahead of its use (the
+    // weights are read-only and the same for every frame of the launch, so a load may be issued
+    // before the barrier that ends the stage using the previous pair): w[k], w[k+1] of stage s
+    auto wpair = [&](int s, int k) { return ld_pair(wt + (s * NH + q) * 4 + k); };
+    float2 wc = wpair(0, 0);
     while (true) {
         if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
         bar(bid, tps);
@@ -554,6 +565,8 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         // forward recomputation of iteration it
 #pragma unroll
         for (int s = 0; s < n; ++s) {
+            const float2 w2 = wc;
+            wc = s + 1 < n ? wpair(s + 1, 0) : wpair(n - 1, last ? 0 : 2);   // next: this sweep, the R sweep or the adjoint of the L sweep
             if (act) {
                 const int p = n - 1 - s;
                 const float* Ls = L + s * N;
@@ -561,7 +574,6 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 float* Lo = L + (s + 1) * N;
                 const int t = ins0(q, p), b = t | (1 << p);
                 const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
-                const float2 w2 = ld_pair(wt + (s * NH + q) * 4);
                 Lo[t] = fw(lt, radd(lb, rb), w2.x);
                 Lo[b] = radd(fw(rt, lt, w2.y), lb);
             }
@@ -570,6 +582,8 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         if (!last) {
 #pragma unroll
             for (int s = n - 1; s >= 1; --s) {
+                const float2 w2 = wc;
+                if (s > 1) wc = wpair(s - 1, 2);          // (stage 1's pair also starts the adjoint of the R sweep)
                 if (act) {
                     const int p = n - 1 - s;
                     const float* Ls = L + s * N;
@@ -577,7 +591,6 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     float* Ro = Rt + (s - 1) * N;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
-                    const float2 w2 = ld_pair(wt + (s * NH + q) * 4 + 2);
                     Ro[t] = fw(rt, radd(lb, rb), w2.x);
                     Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
@@ -591,6 +604,8 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         if (!last) {
 #pragma unroll
             for (int s = 1; s <= n - 1; ++s) {
+                const float2 w2 = wc;
+                wc = s + 1 <= n - 1 ? wpair(s + 1, 2) : wpair(n - 1, 0);     // next: this adjoint or the L sweep's
                 if (act) {
                     const int p = n - 1 - s;
                     const float* gis = G + (s - 1) * N;
@@ -604,7 +619,6 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     const float lt = Ls[t], lb = Ls[b];
                     float ct = 0.f, cb = 0.f;
                     if (gt != 0.f || gb != 0.f) {
-                        const float2 w2 = ld_pair(wt + (s * NH + q) * 4 + 2);   // w[2], w[3]
                         if (gt != 0.f) {                                         // R_out1 = f(a, lb + rb; w2)
                             const float c = radd(lb, rb);
                             const bool amin = fabsf(a) <= fabsf(c);
@@ -638,6 +652,8 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         float* gout = P.gout + size_t(f) * (n - 1) * N;
 #pragma unroll
         for (int s = n - 1; s >= 0; --s) {
+            const float2 w2 = wc;
+            if (s > 0) wc = wpair(s - 1, 0);              // (stage 0's pair also starts the next frame)
             if (act) {
                 const int p = n - 1 - s;
                 const float* Ls = L + s * N;
@@ -652,7 +668,6 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 if (gt != 0.f || gb != 0.f) {
                     const float a = Ls[t], lb = Ls[b];
                     const float rt = Rs[t], rb = Rs[b];
-                    const float2 w2 = ld_pair(wt + (s * NH + q) * 4);           // w[0], w[1]
                     if (gt != 0.f) {                                             // L_out1 = f(a, lb + rb; w0)
                         const float c = radd(lb, rb);
                         const bool amin = fabsf(a) <= fabsf(c);
