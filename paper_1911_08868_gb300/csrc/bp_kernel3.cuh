@@ -508,16 +508,55 @@ __device__ __forceinline__ float2 scale2(float2 alpha2, float2 m, float2 nz2)
     return __ffma2_rn(alpha2, m, nz2);
 }
 
-// One PE layer inside a thread: register e pairs with e | 2^i.  For scaled
-// min-sum and a layer i > 0, the elements with tops e and e+1 (e even) run
-// together: their sums, scalings and final adds as packed two-lane FP32
-// operations, each lane rounded exactly as the scalar __fadd_rn / __fmul_rn
-// of fnode<0>, their signed minima one by one.  Layer 0 pairs e with e+1 and
-// stays scalar.
+// Two lanes of fnode<1> (exact box-plus), each lane computed with exactly the operations of
+// fnode<1>: the packed additions, multiplications and fused multiply-adds round each lane as
+// the scalar ones do, the exponentials, the reciprocal, the minimum and the |x| scalings stay
+// scalar, and every packed product feeds only multiplications or is a multiplicand of a
+// multiply-add, so none can be fused into an addition.  a - b is a + (-b), as IEEE subtraction is.
+__device__ __forceinline__ float2 boxplus2(float2 a, float2 b)
+{
+    constexpr float kNegLog2e = -1.44269504088896341f;
+    const float2 sm = make_float2(signed_min(a.x, b.x), signed_min(a.y, b.y));
+    const float2 sum = __fadd2_rn(a, b), dif = __fadd2_rn(a, make_float2(-b.x, -b.y));
+    const float2 p = make_float2(ex2_approx(__fmul_rn(fabsf(sum.x), kNegLog2e)),
+                                 ex2_approx(__fmul_rn(fabsf(sum.y), kNegLog2e)));
+    const float2 q = make_float2(ex2_approx(__fmul_rn(fabsf(dif.x), kNegLog2e)),
+                                 ex2_approx(__fmul_rn(fabsf(dif.y), kNegLog2e)));
+    const float2 den = __fadd2_rn(make_float2(2.f, 2.f), __fadd2_rn(p, q));
+    const float2 sv = __fmul2_rn(__fadd2_rn(p, make_float2(-q.x, -q.y)),
+                                 make_float2(rcp_approx(den.x), rcp_approx(den.y)));
+    const float2 z = __fmul2_rn(sv, sv);
+    float2 h = make_float2(1.f / 13.f, 1.f / 13.f);
+    h = __ffma2_rn(h, z, make_float2(1.f / 11.f, 1.f / 11.f));
+    h = __ffma2_rn(h, z, make_float2(1.f / 9.f, 1.f / 9.f));
+    h = __ffma2_rn(h, z, make_float2(1.f / 7.f, 1.f / 7.f));
+    h = __ffma2_rn(h, z, make_float2(1.f / 5.f, 1.f / 5.f));
+    h = __ffma2_rn(h, z, make_float2(1.f / 3.f, 1.f / 3.f));
+    h = __ffma2_rn(h, z, make_float2(1.f, 1.f));
+    const float2 v = __ffma2_rn(__fmul2_rn(make_float2(2.f, 2.f), sv), h, sm);
+    return make_float2(isinf(sm.x) ? sm.x : v.x, isinf(sm.y) ? sm.y : v.y);
+}
+
+// f of two lanes for the packed PE layers: scaled min-sum (scale2) or exact box-plus (boxplus2).
+template <int FK>
+__device__ __forceinline__ float2 fnode2(float2 a, float2 b, float2 alpha2, float2 nz2)
+{
+    if constexpr (FK == 0) {
+        return scale2(alpha2, make_float2(signed_min(a.x, b.x), signed_min(a.y, b.y)), nz2);
+    } else {
+        return boxplus2(a, b);
+    }
+}
+
+// One PE layer inside a thread: register e pairs with e | 2^i.  For a layer
+// i > 0, the elements with tops e and e+1 (e even) run together: their sums,
+// f (fnode2) and final adds as packed two-lane FP32 operations, each lane
+// rounded exactly as the scalar operations of fnode<FK> and __fadd_rn.
+// Layer 0 pairs e with e+1 and stays scalar.
 template <int E, int FK>
 __device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float alpha, float nz)
 {
-    if (FK == 0 && i > 0) {
+    if (i > 0) {
         const float2 a2 = make_float2(alpha, alpha), nz2 = make_float2(nz, nz);
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
@@ -525,8 +564,8 @@ __device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float 
             const int eb = e | (1 << i);
             const float2 lt = make_float2(x[e], x[e + 1]), lb = make_float2(x[eb], x[eb + 1]);
             const float2 s = __fadd2_rn(lb, make_float2(rv[eb], rv[eb + 1]));
-            const float2 top = scale2(a2, make_float2(signed_min(lt.x, s.x), signed_min(lt.y, s.y)), nz2);
-            const float2 g = scale2(a2, make_float2(signed_min(rv[e], lt.x), signed_min(rv[e + 1], lt.y)), nz2);
+            const float2 top = fnode2<FK>(lt, s, a2, nz2);
+            const float2 g = fnode2<FK>(make_float2(rv[e], rv[e + 1]), lt, a2, nz2);
             const float2 bot = __fadd2_rn(g, lb);
             x[e] = top.x;
             x[e + 1] = top.y;
@@ -548,7 +587,7 @@ __device__ __forceinline__ void l_layer(float* x, const float* rv, int i, float 
 template <int E, int FK>
 __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float alpha, float nz)
 {
-    if (FK == 0 && i > 0) {
+    if (i > 0) {
         const float2 a2 = make_float2(alpha, alpha), nz2 = make_float2(nz, nz);
 #pragma unroll
         for (int e = 0; e < E; e += 2) {
@@ -556,8 +595,8 @@ __device__ __forceinline__ void r_layer(float* y, const float* lv, int i, float 
             const int eb = e | (1 << i);
             const float2 rt = make_float2(y[e], y[e + 1]), rb = make_float2(y[eb], y[eb + 1]);
             const float2 s = __fadd2_rn(make_float2(lv[eb], lv[eb + 1]), rb);
-            const float2 top = scale2(a2, make_float2(signed_min(rt.x, s.x), signed_min(rt.y, s.y)), nz2);
-            const float2 g = scale2(a2, make_float2(signed_min(rt.x, lv[e]), signed_min(rt.y, lv[e + 1])), nz2);
+            const float2 top = fnode2<FK>(rt, s, a2, nz2);
+            const float2 g = fnode2<FK>(rt, make_float2(lv[e], lv[e + 1]), a2, nz2);
             const float2 bot = __fadd2_rn(g, rb);
             y[e] = top.x;
             y[e + 1] = top.y;
