@@ -242,16 +242,11 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
         copy_wait();
         bar(bid, tps);
         for (int it = 0; it < P.T; ++it) {
-            // the thread's weight pairs, each loaded one stage ahead of its use (read-only data,
-            // so the load may be issued before the barrier that ends the previous stage)
             const float* wq = P.w + size_t(it) * n * NH * 4 + size_t(q) * 4;
-            float2 wc = ld_pair(wq);
 #pragma unroll
             for (int s = 0; s < n; ++s) {
-                const float2 w2 = wc;                          // k = 0, 1
-                if (s + 1 < n) wc = ld_pair(wq + (s + 1) * NH * 4);
-                else if (it + 1 < P.T) wc = ld_pair(wq + (n - 1) * NH * 4 + 2);
                 if (act) {
+                    const float2 w2 = ld_pair(wq + s * NH * 4);   // k = 0, 1
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float* Ls = L + s * N;
@@ -266,9 +261,8 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
             if (it == P.T - 1) break;
 #pragma unroll
             for (int s = n - 1; s >= 1; --s) {
-                const float2 w2 = wc;                          // k = 2, 3
-                if (s > 1) wc = ld_pair(wq + (s - 1) * NH * 4 + 2);
                 if (act) {
+                    const float2 w2 = ld_pair(wq + s * NH * 4 + 2);   // k = 2, 3
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float* Ls = L + s * N;
