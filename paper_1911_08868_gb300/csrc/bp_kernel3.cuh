@@ -59,7 +59,12 @@
 // interior R messages go back to their canonical shared-memory planes with
 // the old partition, the planes are reset as in the stage-grouped kernel, and
 // the caches and interior levels are loaded again with the new partition.  A
-// new frame starts from zeroed planes the same way.
+// new frame starts from zeroed planes the same way (a frame on the no-event
+// partition, the usual case, zeroes only the R planes of its group boundaries
+// and restarts its TMEM interiors).  At a switch the first warp builds the
+// partition while the others reset the subgraph being left, and in slots of
+// four warps or more the second warp draws the next switch's event ahead (the
+// draws depend only on the seed, the frame and the event index).
 //
 // One CTA per SM (its shared memory exceeds half an SM's) allocates all 512
 // TMEM columns for its lifetime, so allocations never wait on one another.
