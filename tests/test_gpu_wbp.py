@@ -76,14 +76,16 @@ def test_gradcheck_fp64_kernels(pcbp, oracle, N, K, T, B):
     assert torch.autograd.gradcheck(loss, (l, ww), eps=1e-7, atol=1e-6, rtol=1e-5)
 
 
-@pytest.mark.parametrize("case", [(32, 16, 6, 40), (256, 128, 10, 64), (1024, 512, 6, 24)],
-                         ids=lambda c: f"N{c[0]}")
+@pytest.mark.parametrize("case", [(32, 16, 6, 40), (256, 128, 10, 64), (1024, 512, 6, 24),
+                                  (256, 128, 4, 1000), (1024, 512, 3, 400)],
+                         ids=lambda c: f"N{c[0]}-B{c[3]}")
 def test_fp32_kernels_match_fp32_reference(pcbp, oracle, case):
     """FP32 kernels against the same reference evaluated in FP32: identical
     operation order, so the logits match exactly and the gradients differ
     only in summation order.  Against FP64, min-sum near-ties resolve
     differently in a few processing elements (the gradient is rerouted), so
-    that comparison is loose."""
+    that comparison is loose.  The larger batches give every frame slot several
+    frames in turn."""
     N, K, T, B = case
     fr, pay, llr, w = setup(oracle, N, K, B, T, seed=99)
     code = pcbp.pc_construct(N, K)
