@@ -239,44 +239,61 @@ def test_repeated_calls_are_deterministic(pcbp, oracle):
             assert np.array_equal(first[i], again[i])
 
 
-def test_full_size_workload_sampled(pcbp, oracle):
-    """The benchmark's launch: 2^20 frames, N = 1024, K = 512 (CRC-24), PP-BP
-    s = 4, T = 10, max 300 iterations, Eb/N0 3 dB.  Codewords come from a
-    pool the oracle encodes, noise from torch's device generator; 256 sampled
-    frames are decoded one by one by the oracle and must match bit for bit."""
+def _full_size_sampled(pcbp, oracle, sched_kw, max_iters, ebn0, seed, fer_max):
+    """2^20 frames of N = 1024, K = 512 (CRC-24) in one launch.  Codewords come from a pool the
+    oracle encodes, noise from torch's device generator.  The frames checked one by one against
+    the oracle: 192 drawn at random, the first and the last, the 16 that ran the most iterations
+    (each through many switches) and 16 more that switched at least once and then stopped."""
     import torch
 
     dev = gpu_device()
-    N, K, r, B, max_iters = 1024, 512, 24, 1 << 20, 300
+    N, K, r, B = 1024, 512, 24, 1 << 20
     _, fr = oracle.construct(N, K)
     pool = 1024
-    pay = inputs.payload_numpy(2024, pool, K - r)
+    pay = inputs.payload_numpy(seed, pool, K - r)
     xpool = torch.from_numpy(oracle.encode_frames(pay, fr, r, POLY24)).to(dev)
     idx = torch.arange(B, device=dev) % pool
-    gen = torch.Generator(device=dev).manual_seed(2024)
-    llr = inputs.bpsk_awgn_llr_torch(xpool[idx], gen, inputs.sigma2_of(3.0, K, r, N)).contiguous()
+    gen = torch.Generator(device=dev).manual_seed(seed)
+    llr = inputs.bpsk_awgn_llr_torch(xpool[idx], gen, inputs.sigma2_of(ebn0, K, r, N)).contiguous()
     code = pcbp.pc_construct(N, K, r, POLY24)
-    s = pcbp.sched(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10, seed=3, stop_kind=1)
+    s = pcbp.sched(**sched_kw)
     dec = pcbp.Decoder(code, s, max_iters, dev)
     bits, iters, ok = dec(llr)
     torch.cuda.synchronize()
-    sample = np.random.default_rng(0).choice(B, 256, replace=False)
-    sample[:2] = [0, B - 1]
+    it = iters.cpu().numpy()
+    first_switch = s.T0 if s.mode == 1 else s.it_reset_full
+    rng = np.random.default_rng(0)
+    longest = np.argsort(-it, kind="stable")[:16]
+    switched = np.flatnonzero((it > first_switch) & (it < max_iters))
+    mid = rng.choice(switched, min(16, len(switched)), replace=False) if len(switched) else switched
+    sample = np.unique(np.concatenate([rng.choice(B, 192, replace=False), [0, B - 1], longest, mid]))
+    assert it[longest].max() > 3 * first_switch        # frames that went through several switches
     h_llr = llr[torch.from_numpy(sample).to(dev)].cpu().numpy()
     gb = pcbp.unpack_bits(bits[torch.from_numpy(sample).to(dev)], K).cpu().numpy()
     os_ = osched(oracle, s)
     for j, b in enumerate(sample):
         ref = oracle.decode(fr, r, POLY24, h_llr[j], os_, max_iters, frame_id=int(b))
-        assert int(iters[b]) == ref.iters and int(ok[b]) == ref.crc_ok
-        assert np.array_equal(gb[j], oracle.info_bits(ref.uhat, fr))
-    # whole-batch properties: every frame decoded, iterations within bounds,
-    # and the payload recovered on nearly all frames at 3 dB
-    it = iters.cpu().numpy()
+        assert int(iters[b]) == ref.iters and int(ok[b]) == ref.crc_ok, f"frame {b}"
+        assert np.array_equal(gb[j], oracle.info_bits(ref.uhat, fr)), f"frame {b}"
+    # whole-batch properties: every frame decoded, iterations within bounds, and the payload
+    # recovered on nearly all frames
     assert it.min() >= 1 and it.max() <= max_iters
     got = pcbp.unpack_bits(bits, K)[:, : K - r]
     want = torch.from_numpy(pay).to(dev)[idx]
     fer = (got != want).any(dim=1).float().mean().item()
-    assert fer < 0.05
+    assert fer < fer_max
+
+
+def test_full_size_workload_sampled(pcbp, oracle):
+    """The benchmark's launch: PP-BP s = 4, T = 10, max 300 iterations, Eb/N0 3 dB."""
+    _full_size_sampled(pcbp, oracle, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10, seed=3,
+                                          stop_kind=1), 300, 3.0, 2024, 0.05)
+
+
+def test_full_size_fpbp_sampled(pcbp, oracle):
+    """FP-BP at the same size: 10 stage orders of 100 iterations each (max 1000), Eb/N0 2.5 dB."""
+    _full_size_sampled(pcbp, oracle, dict(mode=2, q_max=10, it_reset_full=100, seed=2, stop_kind=1),
+                       1000, 2.5, 2025, 0.15)
 
 
 # --------------------------------------------------------------------------- the two production kernels
