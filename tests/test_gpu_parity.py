@@ -239,15 +239,15 @@ def test_repeated_calls_are_deterministic(pcbp, oracle):
             assert np.array_equal(first[i], again[i])
 
 
-def _full_size_sampled(pcbp, oracle, sched_kw, max_iters, ebn0, seed, fer_max):
-    """2^20 frames of N = 1024, K = 512 (CRC-24) in one launch.  Codewords come from a pool the
+def _full_size_sampled(pcbp, oracle, sched_kw, max_iters, ebn0, seed, fer_max, N=1024, B=1 << 20):
+    """B frames of length N, K = N/2 (CRC-24) in one launch.  Codewords come from a pool the
     oracle encodes, noise from torch's device generator.  The frames checked one by one against
     the oracle: 192 drawn at random, the first and the last, the 16 that ran the most iterations
     (each through many switches) and 16 more that switched at least once and then stopped."""
     import torch
 
     dev = gpu_device()
-    N, K, r, B = 1024, 512, 24, 1 << 20
+    K, r = N // 2, 24
     _, fr = oracle.construct(N, K)
     pool = 1024
     pay = inputs.payload_numpy(seed, pool, K - r)
@@ -288,6 +288,15 @@ def test_full_size_workload_sampled(pcbp, oracle):
     """The benchmark's launch: PP-BP s = 4, T = 10, max 300 iterations, Eb/N0 3 dB."""
     _full_size_sampled(pcbp, oracle, dict(mode=1, rho_range_fixed=4, P_level=9, N_min=10, T0=10, seed=3,
                                           stop_kind=1), 300, 3.0, 2024, 0.05)
+
+
+@pytest.mark.parametrize("N,B", [(512, 1 << 20), (2048, 1 << 19)])
+def test_full_size_other_lengths_sampled(pcbp, oracle, N, B):
+    """The benchmark's schedule at the other lengths of the PP-BP configuration (N = 512 and
+    2048, K = N/2, CRC-24), 2^20 and 2^19 frames."""
+    n = N.bit_length() - 1
+    _full_size_sampled(pcbp, oracle, dict(mode=1, rho_range_fixed=4, P_level=n - 1, N_min=10, T0=10, seed=3,
+                                          stop_kind=1), 300, 2.75, 2026 + n, 0.1, N=N, B=B)
 
 
 def test_full_size_fpbp_sampled(pcbp, oracle):
