@@ -413,7 +413,8 @@ __device__ __forceinline__ void tm_fence(int* v)
     for (int e = 0; e < E; ++e) asm volatile("" : "+r"(v[e]));
 }
 
-// Packs the partition for the sweeps (slot leader, after build_groups).
+// Packs the partition for the sweeps (one thread, after build_groups: the no-event template
+// and the partition self-check; switches use build_partition_warp).
 template <int LOGN, int KB>
 __device__ __noinline__ void pack_groups(Ctl3<LOGN, KB>* c)
 {
