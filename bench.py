@@ -59,13 +59,6 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-wbp", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--sweep", action="store_true",
-                    help="FER curves over Eb/N0 1.5..4.0 dB instead of the benchmark line")
-    ap.add_argument("--sweep-frames", type=int, default=1_000_000)
-    ap.add_argument("--sweep-n", type=int, default=1024, choices=(512, 1024, 2048),
-                    help="code length of the sweep (K = N/2, CRC-24); N != 1024 runs the s=4 T=10 PP-BP, "
-                         "FP-BP and plain BP schedules only")
-    ap.add_argument("--sweep-oracle-frames", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -451,84 +444,6 @@ def boxplus_oracle_check(sample, gpu_row):
             "identical_iterations": float(np.mean(it == sample["iters"])), "dtype": "f64"}
 
 
-SWEEP_EBN0 = tuple(1.5 + 0.25 * i for i in range(11))
-SWEEP_SCHEDULES = {f"ppbp_s{s_}_t{t_}": dict(mode=1, rho_range_fixed=s_, P_level=9, N_min=t_, D=0, T0=t_, stop_from=1,
-                                             stop_kind=1, alpha=0.9375, seed=3)
-                   for s_ in (3, 4, 5) for t_ in (5, 10, 20)}
-SWEEP_SCHEDULES["fpbp_q10_t100"] = VARIANTS["fpbp_q10_t100"]
-SWEEP_SCHEDULES["plain_bp"] = VARIANTS["plain_bp"]
-SWEEP_ORACLE = ("ppbp_s4_t10", "fpbp_q10_t100")
-
-
-def run_sweep(args):
-    """FER and mean iterations of the PP-BP grid (s in {3,4,5}, T in {5,10,20}), FP-BP and plain BP
-    at Eb/N0 1.5..4.0 dB on the benchmark code; for the benchmark schedule and FP-BP, the oracle
-    decodes the first frames of every point too (same frame ids): its FER interval, and whether its
-    decisions and iteration counts equal the GPU's on those frames."""
-    import numpy as np
-    import torch
-
-    import oracle as O
-    from paper_1911_08868_gb300 import _build
-
-    _build.build()
-    from paper_1911_08868_gb300 import inputs, pcbp
-
-    dev = torch.device("cuda", 0)
-    B, Bo = args.sweep_frames, args.sweep_oracle_frames
-    N, K = args.sweep_n, args.sweep_n // 2          # the sweep's code (the benchmark code by default)
-    n = N.bit_length() - 1
-    schedules = {k: dict(v) for k, v in SWEEP_SCHEDULES.items()}
-    if N != 1024:
-        schedules = {k: v for k, v in schedules.items() if k in ("ppbp_s4_t10", "fpbp_q10_t100", "plain_bp")}
-    for v in schedules.values():
-        if v.get("mode") == 1:
-            v["P_level"] = n - 1
-    code = pcbp.pc_construct(N, K, R_CRC, POLY)
-    _, fr = O.construct(N, K)
-    threads = O.max_threads()
-    rows = []
-    for ebn0 in SWEEP_EBN0:
-        gen = torch.Generator(device=dev).manual_seed(5000 + int(round(ebn0 * 100)))
-        pay = inputs.payload_torch(gen, B, K - R_CRC, dev)
-        x = torch.empty((B, N), dtype=torch.uint8, device=dev)
-        pcbp.pc_encode(code, pay, x)
-        llr = inputs.bpsk_awgn_llr_torch(x, gen, inputs.sigma2_of(ebn0, K, R_CRC, N)).contiguous()
-        del x
-        sub_llr = llr[:Bo].cpu().numpy()
-        sub_pay = pay[:Bo].cpu().numpy()
-        for name, kw in schedules.items():
-            max_iters = VARIANT_MAX_ITERS.get(name, MAX_ITERS)
-            dec = pcbp.Decoder(code, pcbp.sched(**kw), max_iters, dev)
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record()
-            dec(llr)
-            t1.record()
-            torch.cuda.synchronize()
-            got = pcbp.unpack_bits(dec.bits, K)[:, : K - R_CRC]
-            errors = int((got != pay).any(dim=1).sum().item())
-            row = {"schedule": name, "ebn0_db": ebn0, "frames": B, "fer": errors / B, "errors": errors,
-                   "fer_ci95": wilson(errors, B), "mean_iters": float(dec.iters.double().mean().item()),
-                   "gbit_s": B * (K - R_CRC) / (t0.elapsed_time(t1) / 1e3) / 1e9}
-            if name in SWEEP_ORACLE:
-                os_ = O.Sched(**kw)
-                u, it, ok = O.decode_batch(fr, R_CRC, POLY, sub_llr, os_, max_iters, nthreads=threads)
-                ogot = O.info_bits(u, fr)[:, : K - R_CRC]
-                oerr = int((ogot != sub_pay).any(axis=1).sum())
-                oci = wilson(oerr, Bo)
-                gsub = got[:Bo].cpu().numpy()
-                gits = dec.iters[:Bo].cpu().numpy()
-                row["oracle"] = {"frames": Bo, "fer": oerr / Bo, "fer_ci95": oci, "mean_iters": float(it.mean()),
-                                 "identical_decisions": bool(np.array_equal(ogot, gsub)),
-                                 "identical_iterations": bool(np.array_equal(it, gits)),
-                                 "intervals_overlap": bool(oci[0] <= row["fer_ci95"][1] and row["fer_ci95"][0] <= oci[1])}
-            rows.append(row)
-        del llr, pay
-    print(json.dumps({"sweep": rows, "code": f"N={N} K={K} CRC-24 (0x1B2B117)", "data": "synthetic BPSK/AWGN",
-                      "oracle_cores": threads, "dtype": "f32"}), flush=True)
-
-
 def wbp_loss(logits, bits):
     import torch
 
@@ -865,11 +780,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if needs_spawn(args.gpus) and not args.sweep:
+    if needs_spawn(args.gpus):
         sys.exit(spawn_ranks(args.gpus, str(Path(__file__).resolve()), sys.argv[1:]))
-    if args.sweep:
-        run_sweep(args)
-    elif args.impl == "reference":
+    if args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
