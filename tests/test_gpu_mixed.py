@@ -167,3 +167,35 @@ def test_slot_limit_is_what_a_launch_uses(pcbp, oracle):
     with pytest.raises(pcbp.PcError) as e:
         pcbp.bp_slot_limit(parts[0][0], 96)
     assert e.value.status == pcbp.PC_EUNSUPPORTED
+
+
+def test_all_lengths_rates_and_variants_in_one_table(pcbp, oracle):
+    """Every TMEM length at three rates, with scaled min-sum and box-plus batches and the CRC,
+    G-matrix and combined stops, in one table beside an N = 64 batch of the shared-memory kernel:
+    every batch equals bp_decode alone."""
+    import torch
+
+    dev = gpu_device()
+    sizes = [(N, R) for N in (2048, 1024, 512, 256, 128) for R in (0.25, 0.5, 0.75)] + [(64, 0.5)]
+    parts, _ = make_parts(pcbp, oracle, dev, sizes, 160, seed=211)
+    for i, (code, sch, max_iters, llr, slots) in enumerate(parts):
+        n = code.n
+        if i % 4 == 1:
+            sch = pcbp.sched(mode=1, rho_range_fixed=3, P_level=n - 1, N_min=5, T0=5, seed=9 + i, stop_kind=1,
+                             fkind=1)
+            max_iters = 40
+        elif i % 4 == 2:
+            sch = pcbp.sched(mode=1, rho_range_fixed=4, P_level=n - 1, N_min=10, T0=10, seed=9 + i,
+                             stop_kind=3, stop_from=2)
+        elif i % 4 == 3:
+            sch = pcbp.sched(mode=2, q_max=10, it_reset_full=30, seed=9 + i, stop_kind=2, stop_from=3, fkind=1)
+            max_iters = 40
+        parts[i] = (code, sch, max_iters, llr, slots)
+    md = pcbp.MixedDecoder(parts, dev)
+    bits, iters, ok = md()
+    torch.cuda.synchronize()
+    want = per_batch(pcbp, parts)
+    for i in range(len(parts)):
+        assert torch.equal(bits[i], want[i][0]), sizes[i]
+        assert torch.equal(iters[i], want[i][1]), sizes[i]
+        assert torch.equal(ok[i], want[i][2]), sizes[i]
