@@ -87,6 +87,17 @@ __device__ __forceinline__ void bar(unsigned id, unsigned count)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Synchronisation of a frame slot between the stage just done (butterfly distance 2^pd) and the
+// next step (2^pn; kCross when it reads across warps).  One thread per processing element q:
+// in a stage of distance 2^p <= 32 the elements q = 32w .. 32w+31 of warp w touch exactly the
+// positions [64w, 64w+64), so between two such stages a warp exchanges data only with itself.
+constexpr int kCross = 99;
+__device__ __forceinline__ void stage_sync(int pd, int pn, unsigned id, unsigned count)
+{
+    if (pd <= 5 && pn <= 5) __syncwarp();
+    else bar(id, count);
+}
+
 // Two consecutive weights (k, k+1) of one processing element in one load
 // (the weight array is 8-byte aligned for float, 16-byte for double).
 __device__ __forceinline__ float2 ld_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
@@ -256,7 +267,9 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                     Lo[t] = fw(lt, radd(lb, rb), w2.x);
                     Lo[b] = radd(fw(rt, lt, w2.y), lb);
                 }
-                bar(bid, tps);
+                // after the last stage: the R sweep's first stage, or the logits read across warps
+                const int p = n - 1 - s;
+                stage_sync(p, s < n - 1 ? p - 1 : (it == P.T - 1 ? kCross : 0), bid, tps);
             }
             if (it == P.T - 1) break;
 #pragma unroll
@@ -272,11 +285,14 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                     Ro[t] = fw(rt, radd(lb, rb), w2.x);
                     Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
-                bar(bid, tps);
+                // after the last stage: the checkpoint copy reads across warps
+                const int p = n - 1 - s;
+                stage_sync(p, s > 1 ? p + 1 : kCross, bid, tps);
             }
             if (P.ckpt) {
                 // no barrier after the copy: the R planes are next written by the R sweep of
-                // the next iteration, n slot barriers later
+                // the next iteration, after the slot barrier that ends the first stage of its L
+                // sweep (distance 2^(n-1) > 32 from N = 128; below, the slot is one warp)
                 float4* dst = reinterpret_cast<float4*>(P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N);
                 const float4* src = reinterpret_cast<const float4*>(R);
                 for (int j = tid; j < (n - 1) * N / 4; j += tps) dst[j] = src[j];
@@ -496,11 +512,15 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
 // values) in registers over all the frames it handles and adds it to gw once at the end, so the
 // shared memory that the accumulator takes in the kernel above holds, per frame slot, the
 // incoming gradient planes (levels 2..n, copied with cp.async when the frame starts instead of
-// read from global memory at every stage of the R-sweep adjoint) and a second copy of R(it)
-// (levels 2..n, for the adjoint of the L sweep, instead of copying the checkpoint again).  The
-// arithmetic of every stage is the kernel above's.
-// Per slot: L levels 1..n+1, R levels 2..n+1, the gradient of L at levels 1..n+1, two gradient
-// planes between R levels, G (n-1 planes), R0 (n-1 planes): (5n+2) N floats.
+// read from global memory at every stage of the R-sweep adjoint) and a second set of R planes.
+// The arithmetic of every stage is the kernel above's.
+// Per slot: L levels 1..n (plane n unused: L level n+1 is not needed), R(it) (the checkpoint,
+// levels 2..n), R(it+1) recomputed (levels 2..n) and the priors (level n+1), the gradient of L
+// at levels 1..n+1, two gradient planes between R levels and G, the incoming gradient (levels
+// 2..n): (5n+2) N floats.  Between two stages of butterfly distance at most 32 a warp waits only
+// for itself (stage_sync); the gradient planes are left zero by the stage that consumes them, so
+// a frame starts without clearing them; the next frame's index and this frame's accumulated LLR
+// gradient are read early and used later, so neither round trip stalls the slot.
 template <int LOGN>
 __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_constant__ WbpParams<float> P)
 {
@@ -518,15 +538,17 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
     __syncthreads();
     const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
     constexpr size_t slot_reals = size_t(5 * n + 2) * N;
-    float* L = reinterpret_cast<float*>(smem + tab) + size_t(slot) * slot_reals;   // levels 1..n+1
-    float* Rt = L + (n + 1) * N;                                                   // R, levels 2..n+1
-    float* gL = Rt + n * N;                                                        // levels 1..n+1
+    float* const L = reinterpret_cast<float*>(smem + tab) + size_t(slot) * slot_reals;   // levels 1..n
+    float* const Rnw = L + (n + 1) * N;                                                 // R(it+1), levels 2..n
+    float* const Pri = Rnw + (n - 1) * N;                                               // R level n+1
+    float* const gL = Rnw + n * N;                                                      // levels 1..n+1
     float* gA = gL + (n + 1) * N;
     float* gB = gA + N;
-    float* G = gB + N;                                                             // incoming, levels 2..n
-    float* R0 = G + (n - 1) * N;                                                   // R(it), levels 2..n
-    for (int j = tid; j < N; j += tps) Rt[(n - 1) * N + j] = prior_v<float>(s_frozen, j);
-    __shared__ long long s_frame[32];
+    float* const G = gB + N;                                                            // incoming, levels 2..n
+    float* const Rck = G + (n - 1) * N;                                                 // R(it), levels 2..n
+    for (int j = tid; j < N; j += tps) Pri[j] = prior_v<float>(s_frozen, j);
+    for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = 0.f;
+    __shared__ long long s_frame[32], s_next[32];
     const unsigned bid = 1u + unsigned(slot);
     const float* wt = P.w + size_t(it) * n * NH * 4;
     const bool act = tid < NH;                 // N < 64: fewer elements than a warp
@@ -541,54 +563,70 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
     // weights are read-only and the same for every frame of the launch, so a load may be issued
     // before the barrier that ends the stage using the previous pair): w[k], w[k+1] of stage s
     auto wpair = [&](int s, int k) { return ld_pair(wt + (s * NH + q) * 4 + k); };
+    // inputs of frame fx: the checkpoint R(it), the LLRs (L level 1) and (before the last
+    // iteration) the incoming gradient
+    auto fetch = [&](long long fx) {
+        copy_async(Rck, P.ckpt + (size_t(it) * P.B + size_t(fx)) * (n - 1) * N, (n - 1) * N, tid, tps);
+        copy_async(L, P.llr + size_t(fx) * N, N, tid, tps);
+        if (!last) copy_async(G, P.gin + size_t(fx) * (n - 1) * N, (n - 1) * N, tid, tps);
+    };
+    // the next frame's index is taken as a frame starts and published by the slot leader a few
+    // stages later, before the slot barrier that ends the last forward stage of distance 2^6 or
+    // more (or the first stage, where the slot is one warp), so the atomic's round trip overlaps
+    // the stages
+    constexpr int s_pub = n >= 7 ? n - 7 : 0;
     float2 wc = wpair(0, 0);
-    while (true) {
-        if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
-        bar(bid, tps);
-        const long long f = s_frame[slot];
-        if (f >= P.B) break;
-        const float* Rp = P.ckpt + (size_t(it) * P.B + size_t(f)) * (n - 1) * N;   // R(it) before this iteration
-        copy_async(Rt, Rp, (n - 1) * N, tid, tps);
-        copy_async(R0, Rp, (n - 1) * N, tid, tps);
-        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
-        if (!last) copy_async(G, P.gin + size_t(f) * (n - 1) * N, (n - 1) * N, tid, tps);
-        for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = 0.f;
-        for (int j = tid; j < N; j += tps) gA[j] = gB[j] = 0.f;
+    if (tid == 0) s_frame[slot] = (long long)atomicAdd(P.counter, 1ull);
+    bar(bid, tps);
+    long long f = s_frame[slot];
+    while (f < P.B) {
+        unsigned long long nf = 0;
+        if (tid == 0) nf = atomicAdd(P.counter, 1ull);
+        fetch(f);
         copy_wait();
         bar(bid, tps);
-        // forward recomputation of iteration it
+        // forward recomputation of iteration it (L level n+1 is not needed)
 #pragma unroll
-        for (int s = 0; s < n; ++s) {
+        for (int s = 0; s < n - 1; ++s) {
             const float2 w2 = wc;
-            wc = s + 1 < n ? wpair(s + 1, 0) : wpair(n - 1, last ? 0 : 2);   // next: this sweep, the R sweep or the adjoint of the L sweep
+            wc = s + 1 < n - 1 ? wpair(s + 1, 0) : wpair(n - 1, last ? 0 : 2);   // next: this sweep, the R sweep or the adjoint of the L sweep
+            const int p = n - 1 - s;
             if (act) {
-                const int p = n - 1 - s;
                 const float* Ls = L + s * N;
-                const float* Rs = Rt + s * N;                                   // R(it) at level s+2
+                const float* Rs = Rck + s * N;                                  // R(it) at level s+2
                 float* Lo = L + (s + 1) * N;
                 const int t = ins0(q, p), b = t | (1 << p);
                 const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
                 Lo[t] = fw(lt, radd(lb, rb), w2.x);
                 Lo[b] = radd(fw(rt, lt, w2.y), lb);
             }
-            bar(bid, tps);
+            if (s == s_pub && tid == 0) s_next[slot] = (long long)nf;
+            stage_sync(p, p - 1, bid, tps);
+        }
+        const long long fn = s_next[slot];
+        // this frame's accumulated LLR gradient, read now and added after the adjoint of the L sweep
+        float gll[2] = {0.f, 0.f};
+        if (P.gllr) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (tid + h * tps < N) gll[h] = P.gllr[size_t(f) * N + tid + h * tps];
         }
         if (!last) {
 #pragma unroll
             for (int s = n - 1; s >= 1; --s) {
                 const float2 w2 = wc;
                 if (s > 1) wc = wpair(s - 1, 2);          // (stage 1's pair also starts the adjoint of the R sweep)
+                const int p = n - 1 - s;
                 if (act) {
-                    const int p = n - 1 - s;
                     const float* Ls = L + s * N;
-                    const float* Rs = Rt + s * N;
-                    float* Ro = Rt + (s - 1) * N;
+                    const float* Rs = s == n - 1 ? Pri : Rnw + s * N;
+                    float* Ro = Rnw + (s - 1) * N;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
                     Ro[t] = fw(rt, radd(lb, rb), w2.x);
                     Ro[b] = radd(fw(rt, lt, w2.y), rb);
                 }
-                bar(bid, tps);
+                stage_sync(p, s > 1 ? p + 1 : n - 2, bid, tps);
             }
         } else {
             for (int k = tid; k < K; k += tps) gL[n * N + s_info[k]] = P.glogits[size_t(f) * K + k];
@@ -600,15 +638,16 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
             for (int s = 1; s <= n - 1; ++s) {
                 const float2 w2 = wc;
                 wc = s + 1 <= n - 1 ? wpair(s + 1, 2) : wpair(n - 1, 0);     // next: this adjoint or the L sweep's
+                const int p = n - 1 - s;
                 if (act) {
-                    const int p = n - 1 - s;
                     const float* gis = G + (s - 1) * N;
-                    const float* Rs = Rt + s * N;                               // R level s+2
+                    const float* Rs = s == n - 1 ? Pri : Rnw + s * N;           // R level s+2
                     const float* Ls = L + s * N;
                     float* gLs = gL + s * N;
                     const int t = ins0(q, p), b = t | (1 << p);
-                    const float gt = radd(gis[t], gA[t]);                        // gradient of R level s+1
-                    const float gb = radd(gis[b], gA[b]);
+                    // gradient of R level s+1 (stage 1 has no contribution from a previous stage)
+                    const float gt = s == 1 ? gis[t] : radd(gis[t], gA[t]);
+                    const float gb = s == 1 ? gis[b] : radd(gis[b], gA[b]);
                     const float a = Rs[t], rb = Rs[b];
                     const float lt = Ls[t], lb = Ls[b];
                     float ct = 0.f, cb = 0.f;
@@ -635,10 +674,12 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                             else gLs[t] = radd(gLs[t], rmul(rmul(gb, w2.y), sgn(a)));
                         }
                     }
-                    gB[t] = ct;                                                  // contributions to R level s+2
-                    gB[b] = cb;
+                    if (s < n - 1) {                                             // contributions to R level s+2
+                        gB[t] = ct;
+                        gB[b] = cb;
+                    }
                 }
-                bar(bid, tps);
+                stage_sync(p, s < n - 1 ? p - 1 : 0, bid, tps);
                 float* tmp = gA; gA = gB; gB = tmp;
             }
         }
@@ -648,15 +689,17 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         for (int s = n - 1; s >= 0; --s) {
             const float2 w2 = wc;
             if (s > 0) wc = wpair(s - 1, 0);              // (stage 0's pair also starts the next frame)
+            const int p = n - 1 - s;
             if (act) {
-                const int p = n - 1 - s;
                 const float* Ls = L + s * N;
-                const float* Rs = s < n - 1 ? R0 + s * N : Rt + (n - 1) * N;    // R(it) level s+2 (n+1: priors)
+                const float* Rs = s < n - 1 ? Rck + s * N : Pri;                // R(it) level s+2 (n+1: priors)
                 float* gLs = gL + s * N;
-                const float* gLo = gL + (s + 1) * N;
+                float* gLo = gL + (s + 1) * N;
                 float* gos = gout + size_t(s) * N;
                 const int t = ins0(q, p), b = t | (1 << p);
                 const float gt = gLo[t], gb = gLo[b];
+                gLo[t] = 0.f;                                                    // cleared for the next frame
+                gLo[b] = 0.f;
                 float gRt = 0.f, gRb = 0.f;
                 float gat = gLs[t], gab = gLs[b];
                 if (gt != 0.f || gb != 0.f) {
@@ -691,11 +734,18 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     gos[b] = gRb;
                 }
             }
-            bar(bid, tps);
+            stage_sync(p, s > 0 ? p + 1 : kCross, bid, tps);
         }
-        if (P.gllr)
-            for (int j = tid; j < N; j += tps) P.gllr[size_t(f) * N + j] = radd(P.gllr[size_t(f) * N + j], gL[j]);
-        bar(bid, tps);
+        // the gradient of the LLRs (L level 1), then level 1 cleared for the next frame
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = tid + h * tps;
+            if (j < N) {
+                if (P.gllr) P.gllr[size_t(f) * N + j] = radd(gll[h], gL[j]);
+                gL[j] = 0.f;
+            }
+        }
+        f = fn;
     }
     if (act) {
         float* g = P.gw + size_t(it) * n * NH * 4 + size_t(q) * 4;
