@@ -252,12 +252,15 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
             for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = 0.f;
         copy_wait();
         bar(bid, tps);
+        // each stage's weight pair is loaded one stage ahead (read-only, so across the barrier)
+        float2 wc = ld_pair(P.w + size_t(q) * 4);
         for (int it = 0; it < P.T; ++it) {
             const float* wq = P.w + size_t(it) * n * NH * 4 + size_t(q) * 4;
 #pragma unroll
             for (int s = 0; s < n; ++s) {
+                const float2 w2 = wc;                              // k = 0, 1
+                wc = s + 1 < n ? ld_pair(wq + (s + 1) * NH * 4) : (it + 1 < P.T ? ld_pair(wq + (n - 1) * NH * 4 + 2) : wc);
                 if (act) {
-                    const float2 w2 = ld_pair(wq + s * NH * 4);   // k = 0, 1
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float* Ls = L + s * N;
@@ -274,8 +277,9 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
             if (it == P.T - 1) break;
 #pragma unroll
             for (int s = n - 1; s >= 1; --s) {
+                const float2 w2 = wc;                              // k = 2, 3
+                wc = s > 1 ? ld_pair(wq + (s - 1) * NH * 4 + 2) : ld_pair(wq + n * NH * 4);   // then the next iteration's stage 0
                 if (act) {
-                    const float2 w2 = ld_pair(wq + s * NH * 4 + 2);   // k = 2, 3
                     const int p = n - 1 - s;
                     const int t = ins0(q, p), b = t | (1 << p);
                     const float* Ls = L + s * N;
