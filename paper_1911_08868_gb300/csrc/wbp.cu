@@ -98,6 +98,26 @@ __device__ __forceinline__ void stage_sync(int pd, int pn, unsigned id, unsigned
     else bar(id, count);
 }
 
+// Plane layout of the unrolled FP32 kernels: position j lives at element sw32(j), which
+// complements the low five bits of j when its bit 5 is set.  A warp's element pairs of a stage of
+// distance 2^p < 32 cover one block of 64 positions with bit p clear in its two halves; the
+// complement sends the second half to the banks the first half leaves free (bit p set), so no
+// stage has bank conflicts (in a stage of distance >= 32 all 32 positions of a warp share bit 5
+// and the map permutes their banks).  The checkpoints and the gradient planes between backward
+// launches keep this layout in global memory; LLRs, logits, their gradients and the LLR gradient
+// are read and written at their natural positions.  Identity for N <= 32.
+__device__ __forceinline__ int sw32(int j) { return j ^ (((j >> 5) & 1) * 31); }
+
+// Copy the count = N reals of a natural-order row into a plane in the sw32 layout (4-byte
+// cp.async, no register round trip); waited for with copy_wait().
+__device__ __forceinline__ void copy_async_sw(float* dst, const float* src, int count, int tid, int tps)
+{
+    for (int j = tid; j < count; j += tps)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(uint32_t(__cvta_generic_to_shared(dst + sw32(j)))),
+                     "l"(size_t(__cvta_generic_to_global(src + j)))
+                     : "memory");
+}
+
 // Two consecutive weights (k, k+1) of one processing element in one load
 // (the weight array is 8-byte aligned for float, 16-byte for double).
 __device__ __forceinline__ float2 ld_pair(const float* p) { return __ldg(reinterpret_cast<const float2*>(p)); }
@@ -217,7 +237,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_kernel(const __grid_const
 // ---------------------------------------------------------------------------
 // FP32 forward for N <= 1024 with the stage loops unrolled for the length: one thread per
 // processing element (tps = N/2), so every index and plane offset of a stage is a compile-time
-// shift or constant.  Same planes and arithmetic as wbp_forward_kernel.
+// shift or constant.  Same planes (in the sw32 layout) and arithmetic as wbp_forward_kernel.
 template <int LOGN>
 __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_constant__ WbpParams<float> P)
 {
@@ -235,7 +255,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
     const int slot = threadIdx.x / tps, tid = threadIdx.x - slot * tps;
     float* L = reinterpret_cast<float*>(smem + tab + size_t(slot) * size_t(2 * n + 1) * N * sizeof(float));
     float* R = L + (n + 1) * N;                   // plane l-2 = level l, 2 <= l <= n+1
-    for (int j = tid; j < N; j += tps) R[(n - 1) * N + j] = prior_v<float>(s_frozen, j);
+    for (int j = tid; j < N; j += tps) R[(n - 1) * N + sw32(j)] = prior_v<float>(s_frozen, j);
     __shared__ long long s_frame[32];
     const unsigned bid = 1u + unsigned(slot);
     const bool act = tid < NH;                    // N < 64: fewer elements than a warp
@@ -246,7 +266,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
         bar(bid, tps);
         const long long f = s_frame[slot];
         if (f >= P.B) break;
-        copy_async(L, P.llr + size_t(f) * N, N, tid, tps);
+        copy_async_sw(L, P.llr + size_t(f) * N, N, tid, tps);
         for (int j = tid; j < (n - 1) * N; j += tps) R[j] = 0.f;
         if (P.ckpt)
             for (int j = tid; j < (n - 1) * N; j += tps) P.ckpt[size_t(f) * (n - 1) * N + j] = 0.f;
@@ -262,7 +282,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                 wc = s + 1 < n ? ld_pair(wq + (s + 1) * NH * 4) : (it + 1 < P.T ? ld_pair(wq + (n - 1) * NH * 4 + 2) : wc);
                 if (act) {
                     const int p = n - 1 - s;
-                    const int t = ins0(q, p), b = t | (1 << p);
+                    const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                     const float* Ls = L + s * N;
                     const float* Rs = R + s * N;           // level s+2
                     float* Lo = L + (s + 1) * N;
@@ -281,7 +301,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                 wc = s > 1 ? ld_pair(wq + (s - 1) * NH * 4 + 2) : ld_pair(wq + n * NH * 4);   // then the next iteration's stage 0
                 if (act) {
                     const int p = n - 1 - s;
-                    const int t = ins0(q, p), b = t | (1 << p);
+                    const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                     const float* Ls = L + s * N;
                     const float* Rs = R + s * N;           // level s+2
                     float* Ro = R + (s - 1) * N;           // level s+1
@@ -297,12 +317,17 @@ __global__ void __launch_bounds__(1024, 1) wbp_forward_reg_kernel(const __grid_c
                 // no barrier after the copy: the R planes are next written by the R sweep of
                 // the next iteration, after the slot barrier that ends the first stage of its L
                 // sweep (distance 2^(n-1) > 32 from N = 128; below, the slot is one warp)
-                float4* dst = reinterpret_cast<float4*>(P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N);
-                const float4* src = reinterpret_cast<const float4*>(R);
-                for (int j = tid; j < (n - 1) * N / 4; j += tps) dst[j] = src[j];
+                float* dst = P.ckpt + (size_t(it + 1) * P.B + size_t(f)) * (n - 1) * N;
+                if ((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) {
+                    float4* d4 = reinterpret_cast<float4*>(dst);
+                    const float4* s4 = reinterpret_cast<const float4*>(R);
+                    for (int j = tid; j < (n - 1) * N / 4; j += tps) d4[j] = s4[j];
+                } else {
+                    for (int j = tid; j < (n - 1) * N; j += tps) dst[j] = R[j];
+                }
             }
         }
-        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[n * N + s_info[k]];
+        for (int k = tid; k < K; k += tps) P.logits[size_t(f) * K + k] = L[n * N + sw32(s_info[k])];
         bar(bid, tps);
     }
 }
@@ -521,7 +546,7 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
 // Per slot: L levels 1..n (plane n unused: L level n+1 is not needed), R(it) (the checkpoint,
 // levels 2..n), R(it+1) recomputed (levels 2..n) and the priors (level n+1), the gradient of L
 // at levels 1..n+1, two gradient planes between R levels and G, the incoming gradient (levels
-// 2..n): (5n+2) N floats.  Between two stages of butterfly distance at most 32 a warp waits only
+// 2..n): (5n+2) N floats, in the sw32 layout.  Between two stages of butterfly distance at most 32 a warp waits only
 // for itself (stage_sync); the gradient planes are left zero by the stage that consumes them, so
 // a frame starts without clearing them; the next frame's index and this frame's accumulated LLR
 // gradient are read early and used later, so neither round trip stalls the slot.
@@ -550,7 +575,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
     float* gB = gA + N;
     float* const G = gB + N;                                                            // incoming, levels 2..n
     float* const Rck = G + (n - 1) * N;                                                 // R(it), levels 2..n
-    for (int j = tid; j < N; j += tps) Pri[j] = prior_v<float>(s_frozen, j);
+    for (int j = tid; j < N; j += tps) Pri[sw32(j)] = prior_v<float>(s_frozen, j);
     for (int j = tid; j < (n + 1) * N; j += tps) gL[j] = 0.f;
     __shared__ long long s_frame[32], s_next[32];
     const unsigned bid = 1u + unsigned(slot);
@@ -571,7 +596,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
     // iteration) the incoming gradient
     auto fetch = [&](long long fx) {
         copy_async(Rck, P.ckpt + (size_t(it) * P.B + size_t(fx)) * (n - 1) * N, (n - 1) * N, tid, tps);
-        copy_async(L, P.llr + size_t(fx) * N, N, tid, tps);
+        copy_async_sw(L, P.llr + size_t(fx) * N, N, tid, tps);
         if (!last) copy_async(G, P.gin + size_t(fx) * (n - 1) * N, (n - 1) * N, tid, tps);
     };
     // the next frame's index is taken as a frame starts and published by the slot leader a few
@@ -599,7 +624,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 const float* Ls = L + s * N;
                 const float* Rs = Rck + s * N;                                  // R(it) at level s+2
                 float* Lo = L + (s + 1) * N;
-                const int t = ins0(q, p), b = t | (1 << p);
+                const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                 const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
                 Lo[t] = fw(lt, radd(lb, rb), w2.x);
                 Lo[b] = radd(fw(rt, lt, w2.y), lb);
@@ -625,7 +650,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     const float* Ls = L + s * N;
                     const float* Rs = s == n - 1 ? Pri : Rnw + s * N;
                     float* Ro = Rnw + (s - 1) * N;
-                    const int t = ins0(q, p), b = t | (1 << p);
+                    const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                     const float lt = Ls[t], lb = Ls[b], rt = Rs[t], rb = Rs[b];
                     Ro[t] = fw(rt, radd(lb, rb), w2.x);
                     Ro[b] = radd(fw(rt, lt, w2.y), rb);
@@ -633,7 +658,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 stage_sync(p, s > 1 ? p + 1 : n - 2, bid, tps);
             }
         } else {
-            for (int k = tid; k < K; k += tps) gL[n * N + s_info[k]] = P.glogits[size_t(f) * K + k];
+            for (int k = tid; k < K; k += tps) gL[n * N + sw32(s_info[k])] = P.glogits[size_t(f) * K + k];
             bar(bid, tps);
         }
         // adjoint of the R sweep: stage s makes R level s+1 from R level s+2 and L level s+1
@@ -648,7 +673,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     const float* Rs = s == n - 1 ? Pri : Rnw + s * N;           // R level s+2
                     const float* Ls = L + s * N;
                     float* gLs = gL + s * N;
-                    const int t = ins0(q, p), b = t | (1 << p);
+                    const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                     // gradient of R level s+1 (stage 1 has no contribution from a previous stage)
                     const float gt = s == 1 ? gis[t] : radd(gis[t], gA[t]);
                     const float gb = s == 1 ? gis[b] : radd(gis[b], gA[b]);
@@ -700,7 +725,7 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 float* gLs = gL + s * N;
                 float* gLo = gL + (s + 1) * N;
                 float* gos = gout + size_t(s) * N;
-                const int t = ins0(q, p), b = t | (1 << p);
+                const int t = sw32(ins0(q, p)), b = sw32(ins0(q, p) | (1 << p));
                 const float gt = gLo[t], gb = gLo[b];
                 gLo[t] = 0.f;                                                    // cleared for the next frame
                 gLo[b] = 0.f;
@@ -745,8 +770,8 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
         for (int h = 0; h < 2; ++h) {
             const int j = tid + h * tps;
             if (j < N) {
-                if (P.gllr) P.gllr[size_t(f) * N + j] = radd(gll[h], gL[j]);
-                gL[j] = 0.f;
+                if (P.gllr) P.gllr[size_t(f) * N + j] = radd(gll[h], gL[sw32(j)]);
+                gL[sw32(j)] = 0.f;
             }
         }
         f = fn;
@@ -878,9 +903,9 @@ int forward_impl(const pc_code* c, const Real* llr, const Real* w, int32_t T, in
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ws, 0, 8, st) != cudaSuccess) return PC_ECUDA;
     if constexpr (std::is_same<Real, float>::value) {
-        // FP32 up to N = 1024 (from N = 16, with the checkpoints 16-byte aligned: their rows of
-        // (n-1) N floats are copied as float4)
-        if (c->n >= 4 && c->n <= 10 && (reinterpret_cast<uintptr_t>(ckpt) & 15u) == 0)
+        // FP32 from N = 16 to 1024 (the unrolled backward reads its checkpoints in the sw32
+        // layout; at N = 8 that layout is the natural order the generic kernel writes)
+        if (c->n >= 4 && c->n <= 10)
             return launch_forward_reg(c->n, *P, g, st) == cudaSuccess ? PC_OK : PC_ECUDA;
     }
     if (cudaFuncSetAttribute(wbp_forward_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(g.smem)) !=
