@@ -123,3 +123,34 @@ def test_training_lowers_the_loss(pcbp, oracle):
         opt.step()
         losses.append(float(loss.detach()))
     assert np.mean(losses[-5:]) < np.mean(losses[:5])
+
+
+@pytest.mark.parametrize("N,K", [(64, 32), (1024, 512)])
+def test_fp32_unaligned_checkpoint_buffer(pcbp, oracle, N, K):
+    """The unrolled FP32 forward writes its checkpoint rows as float4 into a 16-byte aligned buffer
+    and one float at a time otherwise; both give the backward the same checkpoints: identical
+    logits and LLR gradients, the weight gradient equal up to the order of its atomic sums."""
+    T, B = 4, 48
+    fr, pay, llr, w = setup(oracle, N, K, B, T, seed=5 * N)
+    code = pcbp.pc_construct(N, K)
+    dev = gpu_device()
+    l = llr.to(dev, torch.float32).contiguous()
+    ww = w.to(dev, torch.float32).contiguous()
+    cnt = pcbp.wbp_ckpt_count(code, T, B)
+    ws = torch.empty(pcbp.wbp_workspace_size(code, T, B, 4), dtype=torch.uint8, device=dev)
+    gl = (torch.randn((B, K), generator=torch.Generator().manual_seed(3)) * 1e-2).to(dev)
+    out = []
+    for off in (0, 1):                         # off = 1: the buffer starts 4 bytes past a 16-byte boundary
+        store = torch.zeros(cnt + 4, dtype=torch.float32, device=dev)
+        ckpt = store[off:off + cnt]
+        logits = torch.empty((B, K), dtype=torch.float32, device=dev)
+        pcbp.wbp_forward(code, l, ww, T, logits, ckpt, ws)
+        gw = torch.zeros_like(ww)
+        gllr = torch.empty_like(l)
+        pcbp.wbp_backward(code, l, ww, T, ckpt, gl, gw, gllr, ws)
+        torch.cuda.synchronize()
+        out.append((logits.cpu(), gllr.cpu(), gw.cpu().double()))
+    assert torch.equal(out[0][0], out[1][0])
+    assert torch.equal(out[0][1], out[1][1])
+    assert (out[0][2] - out[1][2]).norm() <= 1e-5 * out[0][2].norm()
+    assert out[0][2].abs().sum() > 0
