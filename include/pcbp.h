@@ -219,12 +219,14 @@ int pc_f_eval(const float* d_a, const float* d_b, float* d_out, int64_t count,
 /* Number of weights, T * n * (N/2) * 4. */
 int wbp_weights_count(const pc_code* code, int32_t T, size_t* count);
 /* Number of checkpoint values, T * B * (n-1) * N (R of levels 2..n after
- * t = 0..T-1 iterations). */
+ * t = 0..T-1 iterations; the values of one level are stored in an internal
+ * position order, so the buffer is meant only for wbp_backward of the same
+ * precision and code). */
 int wbp_ckpt_count(const pc_code* code, int32_t T, int64_t B, size_t* count);
 /* Device workspace bytes of wbp_forward / wbp_backward (real_bytes 4 or 8). */
 int wbp_workspace_size(const pc_code* code, int32_t T, int64_t B, int32_t real_bytes, size_t* bytes);
-/* d_llr [B][N], d_w (wbp_weights_count), d_logits [B][K]; d_ckpt (nullable)
- * receives the checkpoints wbp_backward needs. */
+/* d_llr [B][N], d_w (wbp_weights_count), d_logits [B][K]; d_ckpt (nullable,
+ * 4-byte aligned) receives the checkpoints wbp_backward needs. */
 int wbp_forward(const pc_code* code, const float* d_llr, const float* d_w, int32_t T, int64_t B,
                 float* d_logits, float* d_ckpt, void* d_workspace, void* stream);
 /* Given d_glogits = dLoss/dlogits [B][K]: d_gw += dLoss/dw (caller zeroes it
