@@ -546,10 +546,11 @@ __global__ void __launch_bounds__(1024, 1) wbp_backward_kernel(const __grid_cons
 // Per slot: L levels 1..n (plane n unused: L level n+1 is not needed), R(it) (the checkpoint,
 // levels 2..n), R(it+1) recomputed (levels 2..n) and the priors (level n+1), the gradient of L
 // at levels 1..n+1, two gradient planes between R levels and G, the incoming gradient (levels
-// 2..n): (5n+2) N floats, in the sw32 layout.  Between two stages of butterfly distance at most 32 a warp waits only
-// for itself (stage_sync); the gradient planes are left zero by the stage that consumes them, so
-// a frame starts without clearing them; the next frame's index and this frame's accumulated LLR
-// gradient are read early and used later, so neither round trip stalls the slot.
+// 2..n): (5n+2) N floats, in the sw32 layout.  Between two stages of butterfly distance at most
+// 32 a warp waits only for itself (stage_sync); the gradient planes are left zero by the stage
+// that consumes them, so a frame starts without clearing them; the next frame's index and this
+// frame's accumulated LLR gradient are read early and used later, so neither round trip stalls
+// the slot.
 template <int LOGN>
 __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_constant__ WbpParams<float> P)
 {
