@@ -682,27 +682,30 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                     const float lt = Ls[t], lb = Ls[b];
                     float ct = 0.f, cb = 0.f;
                     if (gt != 0.f || gb != 0.f) {
-                        if (gt != 0.f) {                                         // R_out1 = f(a, lb + rb; w2)
-                            const float c = radd(lb, rb);
-                            const bool amin = fabsf(a) <= fabsf(c);
-                            const float m = amin ? fabsf(a) : fabsf(c);
-                            dwr[s][2] = radd(dwr[s][2], rmul(gt, sgn(a) * sgn(c) * m));
-                            if (amin) {
-                                ct = radd(ct, rmul(rmul(gt, w2.x), sgn(c)));
-                            } else {
-                                const float gc = rmul(rmul(gt, w2.x), sgn(a));
-                                gLs[b] = radd(gLs[b], gc);
-                                cb = radd(cb, gc);
-                            }
-                        }
-                        if (gb != 0.f) {                                         // R_out2 = f(a, lt; w3) + rb
-                            cb = radd(cb, gb);
-                            const bool amin = fabsf(a) <= fabsf(lt);
-                            const float m = amin ? fabsf(a) : fabsf(lt);
-                            dwr[s][3] = radd(dwr[s][3], rmul(gb, sgn(a) * sgn(lt) * m));
-                            if (amin) ct = radd(ct, rmul(rmul(gb, w2.y), sgn(lt)));
-                            else gLs[t] = radd(gLs[t], rmul(rmul(gb, w2.y), sgn(a)));
-                        }
+                        // both operand cases evaluated and the contributions of the case that does
+                        // not apply replaced by exact zeros (adding 0 leaves a sum as it is), so the
+                        // warp does not diverge on which operand is the minimum; a product with a
+                        // zero upstream gradient is never used (it may be 0 * inf)
+                        const bool g1 = gt != 0.f, g2 = gb != 0.f;
+                        // R_out1 = f(a, lb + rb; w2)
+                        const float c = radd(lb, rb);
+                        const bool amin = fabsf(a) <= fabsf(c);
+                        const float m1 = amin ? fabsf(a) : fabsf(c);
+                        const float d1 = rmul(gt, sgn(a) * sgn(c) * m1);
+                        dwr[s][2] = radd(dwr[s][2], g1 ? d1 : 0.f);
+                        const float v1 = rmul(rmul(gt, w2.x), amin ? sgn(c) : sgn(a));
+                        ct = g1 && amin ? v1 : 0.f;
+                        cb = g1 && !amin ? v1 : 0.f;
+                        if (g1 && !amin) gLs[b] = radd(gLs[b], v1);
+                        // R_out2 = f(a, lt; w3) + rb
+                        cb = radd(cb, gb);
+                        const bool amin2 = fabsf(a) <= fabsf(lt);
+                        const float m2 = amin2 ? fabsf(a) : fabsf(lt);
+                        const float d2 = rmul(gb, sgn(a) * sgn(lt) * m2);
+                        dwr[s][3] = radd(dwr[s][3], g2 ? d2 : 0.f);
+                        const float v2 = rmul(rmul(gb, w2.y), amin2 ? sgn(lt) : sgn(a));
+                        ct = radd(ct, g2 && amin2 ? v2 : 0.f);
+                        if (g2 && !amin2) gLs[t] = radd(gLs[t], v2);
                     }
                     if (s < n - 1) {                                             // contributions to R level s+2
                         gB[t] = ct;
@@ -733,29 +736,30 @@ __global__ void __launch_bounds__(512, 1) wbp_backward_reg_kernel(const __grid_c
                 float gRt = 0.f, gRb = 0.f;
                 float gat = gLs[t], gab = gLs[b];
                 if (gt != 0.f || gb != 0.f) {
+                    // both operand cases, the one that does not apply contributing exact zeros
+                    // (as in the adjoint of the R sweep)
                     const float a = Ls[t], lb = Ls[b];
                     const float rt = Rs[t], rb = Rs[b];
-                    if (gt != 0.f) {                                             // L_out1 = f(a, lb + rb; w0)
-                        const float c = radd(lb, rb);
-                        const bool amin = fabsf(a) <= fabsf(c);
-                        const float m = amin ? fabsf(a) : fabsf(c);
-                        dwr[s][0] = radd(dwr[s][0], rmul(gt, sgn(a) * sgn(c) * m));
-                        if (amin) {
-                            gat = radd(gat, rmul(rmul(gt, w2.x), sgn(c)));
-                        } else {
-                            const float gc = rmul(rmul(gt, w2.x), sgn(a));
-                            gab = radd(gab, gc);
-                            gRb = radd(gRb, gc);
-                        }
-                    }
-                    if (gb != 0.f) {                                             // L_out2 = f(rt, a; w1) + lb
-                        gab = radd(gab, gb);
-                        const bool rmin = fabsf(rt) <= fabsf(a);
-                        const float m = rmin ? fabsf(rt) : fabsf(a);
-                        dwr[s][1] = radd(dwr[s][1], rmul(gb, sgn(rt) * sgn(a) * m));
-                        if (rmin) gRt = radd(gRt, rmul(rmul(gb, w2.y), sgn(a)));
-                        else gat = radd(gat, rmul(rmul(gb, w2.y), sgn(rt)));
-                    }
+                    const bool g1 = gt != 0.f, g2 = gb != 0.f;
+                    // L_out1 = f(a, lb + rb; w0)
+                    const float c = radd(lb, rb);
+                    const bool amin = fabsf(a) <= fabsf(c);
+                    const float m1 = amin ? fabsf(a) : fabsf(c);
+                    const float d1 = rmul(gt, sgn(a) * sgn(c) * m1);
+                    dwr[s][0] = radd(dwr[s][0], g1 ? d1 : 0.f);
+                    const float v1 = rmul(rmul(gt, w2.x), amin ? sgn(c) : sgn(a));
+                    gat = radd(gat, g1 && amin ? v1 : 0.f);
+                    gab = radd(gab, g1 && !amin ? v1 : 0.f);
+                    gRb = g1 && !amin ? v1 : 0.f;
+                    // L_out2 = f(rt, a; w1) + lb
+                    gab = radd(gab, gb);
+                    const bool rmin = fabsf(rt) <= fabsf(a);
+                    const float m2 = rmin ? fabsf(rt) : fabsf(a);
+                    const float d2 = rmul(gb, sgn(rt) * sgn(a) * m2);
+                    dwr[s][1] = radd(dwr[s][1], g2 ? d2 : 0.f);
+                    const float v2 = rmul(rmul(gb, w2.y), rmin ? sgn(a) : sgn(rt));
+                    gRt = g2 && rmin ? v2 : 0.f;
+                    gat = radd(gat, g2 && !rmin ? v2 : 0.f);
                 }
                 gLs[t] = gat;
                 gLs[b] = gab;
