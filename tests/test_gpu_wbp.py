@@ -77,7 +77,8 @@ def test_gradcheck_fp64_kernels(pcbp, oracle, N, K, T, B):
 
 
 @pytest.mark.parametrize("case", [(32, 16, 6, 40), (256, 128, 10, 64), (1024, 512, 6, 24),
-                                  (256, 128, 4, 1000), (1024, 512, 3, 400)],
+                                  (256, 128, 4, 1000), (1024, 512, 3, 400), (128, 64, 5, 300),
+                                  (512, 256, 4, 160)],
                          ids=lambda c: f"N{c[0]}-B{c[3]}")
 def test_fp32_kernels_match_fp32_reference(pcbp, oracle, case):
     """FP32 kernels against the same reference evaluated in FP32: identical
